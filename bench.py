@@ -1,0 +1,311 @@
+#!/usr/bin/env python3
+"""Throughput of the RQMC hot path on GB300: path-steps/s.
+
+Workload (default): LIBOR-market-model caplets, one factor, 40 quarterly
+forwards, flat 5 % curve, 15 % vol, strikes 4.5/5/5.5 %, log-Euler spot-measure
+steps (s = 40), N = 65536 points per replication, M = 64 replications, on the
+three sequences of the comparison (Rasrap, digitally shifted Sobol', Philox),
+FP32 paths with Kahan sums.  One step = one plan execute per sequence
+(3 x N x M x 40 = 503M path-steps).  The result of every timed configuration is
+checked against the FP64 oracle (two replications at full N) before timing.
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the oracle is the reference implementation).
+Under torchrun each rank prices its own replications (seed + rank): weak
+scaling with no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+N_FWD, N_PATHS, M_REPL, SEED = 40, 65536, 64, 1
+SEQS = ("rasrap", "sobol_ds", "philox")
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def lmm_algorithmic_ops(nf, nK, paths):
+    """Source-level operations of one fused caplet launch.
+    MUFU: rcp + ex2 per forward update, lg2 (inverse CDF) + rcp (numeraire) per step.
+    FP32 pipe: 7 per forward update, 16 per inverse CDF, 2 per numeraire step,
+    4 per strike payoff."""
+    upd = nf * (nf + 1) // 2
+    mufu = 2 * upd + 2 * nf
+    fma = 7 * upd + nf * (16 + 2 + 4 * nK)
+    return mufu * paths, fma * paths
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, c[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(k)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_1408_5526_gb300 import inputs, rqmc
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    rqmc.load()
+    lm = inputs.lmm_flat(N_FWD)
+    K = inputs.LMM_STRIKES
+    seed = SEED + rank
+    plans = [rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, s, seed, prec="fp32") for s in SEQS]
+    outs = [torch.empty(p.output_size(), dtype=torch.float64, device=dev) for p in plans]
+    stream = torch.cuda.current_stream()
+
+    # parity gate: the timed configuration must match the oracle (rank 0 checks)
+    parity = None
+    if rank == 0 and not args.skip_parity:
+        import oracle as O
+        worst = 0.0
+        for p, s, o in zip(plans, SEQS, outs):
+            p.execute(o)
+            th = o.cpu().numpy().reshape(M_REPL, -1)
+            q = O.Sequence(rqmc._SEQ[s], N_FWD, M_REPL, seed, joe_kuo=inputs.joe_kuo_table())
+            th_o = O.lmm_caplets(q, lm, K, N_PATHS, m_range=(M_REPL - 1, M_REPL))
+            t = th_o.reshape(1, N_FWD, len(K))
+            scale = np.maximum(np.abs(t), np.abs(t[:, :, 1:2])).reshape(1, -1)
+            worst = max(worst, float(np.max(np.abs(th[M_REPL - 1:] - th_o) / scale)))
+        parity = {"max_scaled_err": worst, "tol": 1e-4, "ok": worst <= 1e-4, "checked": "m=63, all 120 outputs"}
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        for p, o in zip(plans, outs):
+            p.execute(o, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in SEQS]
+           for _ in range(args.steps)]
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(float(k))   # L2 flush outside the timed intervals
+            ev[k][0].record(stream)
+            for j, (p, o) in enumerate(zip(plans, outs)):
+                kev[k][j][0].record(stream)
+                p.execute(o, stream)
+                kev[k][j][1].record(stream)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        time.sleep(0.25)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    launch_ms = [a.elapsed_time(b) for row in kev for a, b in row]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = N_PATHS * M_REPL * N_FWD * len(SEQS) * args.steps * world
+    value = units / (total_ms / 1e3)
+
+    # e2e: the one-shot C-ABI call with host buffers (tables, H2D, kernels, D2H, stats) per sequence
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in SEQS:
+            rqmc.price_caplets(lm, K, N_PATHS, M_REPL, s, seed, prec="fp32")
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = N_PATHS * M_REPL * N_FWD * len(SEQS) * world / (statistics.median(e2e_ms) / 1e3)
+    h2d = 40 * 64 + 40 * 32 * 4   # Halton base constants (Rasrap) + Sobol' direction numbers
+    d2h = len(SEQS) * (M_REPL * N_FWD * len(K) * 8 + 16)
+
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    mufu_peak = 16 * 152 * sm_max * 1e6           # MUFU ops/s: 16 per SM per clock
+    fma_peak = 128 * 152 * sm_max * 1e6           # FP32 lane-ops/s: 128 per SM per clock
+    mufu, fma = lmm_algorithmic_ops(N_FWD, len(K), N_PATHS * M_REPL)
+    per_launch_s = statistics.mean(launch_ms) / 1e3
+    a_mufu, a_fma = mufu / per_launch_s, fma / per_launch_s
+    roof = {"bound": "alu", "pipe": "sfu" if a_mufu / mufu_peak >= a_fma / fma_peak else "fma",
+            "achieved": round(a_mufu / 1e12, 4), "peak": round(mufu_peak / 1e12, 4), "unit": "Tops/s (MUFU)",
+            "frac": round(a_mufu / mufu_peak, 4), "traffic": None,
+            "fma_achieved": round(a_fma / 1e12, 3), "fma_peak": round(fma_peak / 1e12, 3),
+            "fma_frac": round(a_fma / fma_peak, 4),
+            "kernel": "lmm_caplet_kernel<40,float> + theta_kernel",
+            "launch_ms": round(per_launch_s * 1e3, 4),
+            "peak_source": "derived: 16 MUFU / 128 FP32 lanes per SM per clock x 152 SMs x sm_max_mhz"}
+    cpu = cpu_baseline(args) if (rank == 0 and not args.no_cpu) else None
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": "path-steps/s", "value": value, "unit": "path-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "lmm_caplets_40fwd_N65536_M64_rasrap+sobol_ds+philox", "n_fwd": N_FWD,
+                       "N": N_PATHS, "M": M_REPL, "strikes": list(map(float, K)), "sequences": list(SEQS),
+                       "precision": "fp32 paths, Kahan sums, fp64 replication reduction",
+                       "path_steps_per_step": N_PATHS * M_REPL * N_FWD * len(SEQS) * world,
+                       "parallelism": f"replicas x{world} (seed + rank)",
+                       "l2": "flushed (512 MiB write) before every timed step, outside its interval",
+                       "timing": "sum of per-step CUDA-event intervals"},
+            "parity": parity,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "path-steps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms": statistics.median(e2e_ms),
+                    "api": "price_caplets (host buffers) x 3 sequences"},
+            "gpu_launches": args.steps * sum(p.launches() for p in plans),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for p in plans:
+        p.close()
+
+
+def cpu_baseline(args, seconds_hint=True):
+    """The FP64 oracle as it stands, OpenMP over replications, on a bounded sample:
+    Rasrap, full N, one replication per host thread (capped at 16)."""
+    import oracle as O
+    from paper_1408_5526_gb300 import inputs
+    cores = min(O.max_threads(), 16)
+    lm = inputs.lmm_flat(N_FWD)
+    K = inputs.LMM_STRIKES
+    q = O.Sequence(O.RASRAP, N_FWD, M_REPL, SEED)
+    t0 = time.perf_counter()
+    O.lmm_caplets(q, lm, K, N_PATHS, m_range=(0, cores), threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": cores * N_PATHS * N_FWD / dt, "unit": "path-steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"rasrap, {cores} replications x N={N_PATHS} x 40 steps ({dt:.1f} s)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1408_5526_gb300 import inputs
+    cores = min(O.max_threads(), 16)
+    lm = inputs.lmm_flat(N_FWD)
+    K = inputs.LMM_STRIKES
+    n_sample = 8192
+    for _ in range(args.warmup):
+        pass
+    t = []
+    for k in range(args.steps):
+        s = SEQS[k % len(SEQS)]
+        q = O.Sequence({"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX}[s], N_FWD, M_REPL, SEED,
+                       joe_kuo=inputs.joe_kuo_table())
+        t0 = time.perf_counter()
+        O.lmm_caplets(q, lm, K, n_sample, m_range=(0, cores), threads=cores)
+        t.append(time.perf_counter() - t0)
+    units = cores * n_sample * N_FWD
+    value = units * len(t) / sum(t)
+    line = {"impl": "reference", "metric": "path-steps/s", "value": value, "unit": "path-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(t) / len(t),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "lmm_caplets_40fwd_N65536_M64_rasrap+sobol_ds+philox",
+                       "sample": f"{cores} replications x N={n_sample} per step, sequences cycled"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": "path-steps/s",
+                             "sample": f"{cores} replications x N={n_sample} x 40 steps per step"},
+            "e2e": {"value": value, "unit": "path-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--skip-parity", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "ours":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,485 @@
+// api.cu -- the C ABI of librqmc.so (declared in include/rqmc.h): argument validation,
+// plan construction (device tables, model constants, workspace), launches, and the
+// synchronous one-shot estimators.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rqmc_internal.h"
+
+namespace rqmc {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+static std::mutex g_oneshot_mu;
+
+static rqmc_status cuda_fail(cudaError_t e, const char *what) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e));
+    return RQMC_ECUDA;
+}
+
+static bool finite_all(const double *p, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+static void keep_pool_cached(int dev) {
+    static std::once_flag flags[64];
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(flags[dev], [dev]() {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+// ------------------------------------------------------------------ plan construction
+struct ModelHost {
+    std::vector<unsigned char> bytes;   // model tables to copy after the generator tables
+    size_t off = 0;
+};
+
+static rqmc_status common_checks(int s, int64_t N, int64_t offset, int M, int seq, int prec) {
+    if (s < 1 || s > kMaxDims) { set_error("s must be in 1..4096"); return RQMC_EINVAL; }
+    if (N < 1 || N > (int64_t(1) << 31)) { set_error("N must be in 1..2^31"); return RQMC_EINVAL; }
+    if (offset < 0) { set_error("offset must be >= 0"); return RQMC_EINVAL; }
+    if (M < 1 || M > 65535) { set_error("M must be in 1..65535"); return RQMC_EINVAL; }
+    if (seq < 0 || seq > 3) { set_error("unknown sequence"); return RQMC_EINVAL; }
+    if (prec != RQMC_FP64 && prec != RQMC_FP32) { set_error("unknown precision"); return RQMC_EINVAL; }
+    return RQMC_OK;
+}
+
+static void set_reduction(Plan &pl, int nout, int threads, int ppt) {
+    pl.threads = threads;
+    pl.ppt = ppt;
+    pl.nout = nout;
+    RedParams &r = pl.red;
+    r.nout = nout;
+    r.ppt = ppt;
+    r.tile = (uint32_t)(threads * ppt);
+    r.tiles_per_m = (uint32_t)((pl.N + r.tile - 1) / r.tile);
+    r.units = r.tiles_per_m * (uint32_t)pl.M;
+    r.N = (uint32_t)pl.N;
+}
+
+// Allocates one device block: generator tables, model tables, status words, partials
+// (sized for the smallest tile, 32 paths, so launch knobs can change later).
+static rqmc_status finish_plan(Plan *pl, const std::vector<unsigned char> &model, size_t model_align,
+                               size_t partial_doubles, cudaStream_t st, size_t *model_off_out) {
+    Carve cv;
+    GenLayout gl;
+    rqmc_status rs = generator_layout(*pl, cv, gl);
+    if (rs != RQMC_OK) return rs;
+    const size_t model_off = model.empty() ? 0 : cv.take(model.size(), model_align);
+    const size_t status_off = cv.take(sizeof(uint32_t) * 4);
+    const size_t part_off = cv.take(sizeof(double) * std::max<size_t>(partial_doubles, 1));
+    cudaGetDevice(&pl->device);
+    keep_pool_cached(pl->device);
+    pl->d_bytes = cv.off;
+    cudaError_t e = cudaMallocAsync(&pl->d_buf, pl->d_bytes, st);
+    if (e != cudaSuccess) {
+        pl->d_buf = nullptr;
+        set_error(std::string("device allocation failed: ") + cudaGetErrorString(e));
+        return RQMC_ENOMEM;
+    }
+    unsigned char *d = static_cast<unsigned char *>(pl->d_buf);
+    uint32_t *status = reinterpret_cast<uint32_t *>(d + status_off);
+    if ((e = cudaMemsetAsync(status, 0, sizeof(uint32_t) * 4, st)) != cudaSuccess) return cuda_fail(e, "memset");
+    if (!model.empty()) {
+        if ((e = cudaMemcpyAsync(d + model_off, model.data(), model.size(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_fail(e, "model upload");
+    }
+    rs = generator_init(*pl, gl, d, status, st);
+    if (rs != RQMC_OK) {
+        set_error("generator setup launch failed");
+        return rs;
+    }
+    pl->red.partials = reinterpret_cast<double *>(d + part_off);
+    pl->red.status = status + 1;
+    if (model_off_out) *model_off_out = model_off;
+    if (st == 0) {   // plans outlive this call and may run on any stream: finish the setup now
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "plan setup");
+    }
+    return RQMC_OK;
+}
+
+static size_t partial_capacity(const Plan &pl, int nout) {
+    // smallest tile is 32 paths
+    return (size_t)pl.M * (size_t)((pl.N + 31) / 32) * (size_t)nout;
+}
+
+static void destroy(Plan *pl, cudaStream_t st) {
+    if (!pl) return;
+    if (pl->d_buf) cudaFreeAsync(pl->d_buf, st);
+    delete pl;
+}
+
+static int lmm_bucket(int nf) {
+    if (nf <= 16) return 16;
+    if (nf <= 40) return 40;
+    if (nf <= 80) return 80;
+    return 160;
+}
+
+template <typename T>
+static void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK, int bucket) {
+    const double h = p->delta, sh = std::sqrt(p->delta);
+    const double sc = sizeof(T) == 4 ? 1.4426950408889634 : 1.0;   // FP32 uses exp2
+    md = LmmModel<T>{};
+    md.nf = p->n_fwd;
+    md.nK = nK;
+    md.dl = (T)p->delta;
+    md.disc0 = (T)(1.0 / (1.0 + p->delta * p->L0[0]));
+    for (int k = 0; k < nK; ++k) md.K[k] = (T)K[k];
+    const int slot0 = bucket - p->n_fwd;
+    for (int slot = 0; slot < bucket; ++slot) {
+        const int n = slot - slot0 + 1;   // forward index
+        const double L0 = n >= 1 ? p->L0[n] : 0.0;
+        const double sg = n >= 1 ? p->vol[n - 1] : 0.0;
+        md.L0[slot] = (T)L0;
+        md.sg[slot] = (T)sg;
+        md.cdr[slot] = (T)(sg * h * sc);
+        md.cc[slot] = (T)(-0.5 * sg * sg * h * sc);
+        md.cz[slot] = (T)(sg * sh * sc);
+    }
+}
+
+static rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool adjoint) {
+    if (!p || !p->L0 || !p->vol) { set_error("LMM parameters missing"); return RQMC_EINVAL; }
+    if (p->n_fwd < 1 || p->n_fwd > kMaxFwd) { set_error("n_fwd must be in 1..160"); return RQMC_EINVAL; }
+    if (p->n_factors < 1 || p->n_factors > 2 || (!adjoint && p->n_factors != 1)) {
+        set_error(adjoint ? "n_factors must be 1 or 2" : "price_caplets runs one-factor models (n_factors = 1)");
+        return adjoint ? RQMC_EINVAL : RQMC_EUNSUPPORTED;
+    }
+    if (p->n_factors > 1 && !p->loadings) { set_error("loadings required for n_factors > 1"); return RQMC_EINVAL; }
+    if (p->scheme != RQMC_LOG_EULER) { set_error("only the log-Euler scheme is built"); return RQMC_EUNSUPPORTED; }
+    if (!(p->delta > 0.0) || !std::isfinite(p->delta)) { set_error("delta must be > 0"); return RQMC_EINVAL; }
+    if (!finite_all(p->L0, p->n_fwd + 1) || !finite_all(p->vol, p->n_fwd)) {
+        set_error("L0/vol must be finite");
+        return RQMC_EINVAL;
+    }
+    for (int n = 0; n <= p->n_fwd; ++n)
+        if (!(p->L0[n] > -1.0 / p->delta)) { set_error("1 + delta L0 must be positive"); return RQMC_EINVAL; }
+    if (!K || nK < 1 || nK > kMaxStrikes || !finite_all(K, nK)) {
+        set_error("strikes: 1..8 finite values");
+        return RQMC_EINVAL;
+    }
+    if (p->n_fwd * nK > kMaxOutputs) { set_error("n_fwd * n_strikes must be <= 1280"); return RQMC_EINVAL; }
+    return RQMC_OK;
+}
+
+static rqmc_status check_mbs(const rqmc_mbs_params *p) {
+    if (!p) { set_error("MBS parameters missing"); return RQMC_EINVAL; }
+    if (p->months < 1 || p->months > kMaxDims) { set_error("months must be in 1..4096"); return RQMC_EINVAL; }
+    const double v[] = {p->i0, p->K1, p->K2, p->K3, p->K4, p->sigma, p->c};
+    if (!finite_all(v, 7) || p->i0 <= -1.0 || p->sigma < 0.0) { set_error("MBS constants invalid"); return RQMC_EINVAL; }
+    return RQMC_OK;
+}
+
+}  // namespace rqmc
+
+using namespace rqmc;
+
+struct rqmc_plan_s : public Plan {};
+
+// ------------------------------------------------------------------ diagnostics
+extern "C" const char *rqmc_status_string(rqmc_status st) {
+    switch (st) {
+        case RQMC_OK: return "ok";
+        case RQMC_EINVAL: return "invalid argument";
+        case RQMC_ENOMEM: return "out of memory";
+        case RQMC_ECUDA: return "CUDA error";
+        case RQMC_ETIMEOUT: return "device wait timed out";
+        case RQMC_EUNSUPPORTED: return "unsupported request";
+        case RQMC_ENOTABLE: return "Sobol' direction table missing";
+    }
+    return "unknown status";
+}
+extern "C" const char *rqmc_last_error(void) { return g_err.c_str(); }
+extern "C" int rqmc_abi_version(void) { return 1; }
+
+// ------------------------------------------------------------------ plans
+static rqmc_status new_plan(PlanKind kind, int s, int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
+                            rqmc_precision prec, rqmc_plan **out) {
+    rqmc_status rs = common_checks(s, N, offset, M, seq, prec);
+    if (rs != RQMC_OK) return rs;
+    if (!out) { set_error("plan pointer is NULL"); return RQMC_EINVAL; }
+    auto *pl = new rqmc_plan_s();
+    pl->kind = kind;
+    pl->prec = prec;
+    pl->seq = seq;
+    pl->s = s;
+    pl->M = M;
+    pl->N = (uint64_t)N;
+    pl->offset = (uint64_t)offset;
+    pl->seed = seed;
+    pl->inst = 0;
+    *out = pl;
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_plan_product(int s, int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
+                                         const double *a_host, rqmc_precision prec, rqmc_plan **plan) {
+    if (!a_host || !finite_all(a_host, std::max(0, std::min(s, kMaxDims)))) {
+        set_error("a: s finite weights required");
+        return RQMC_EINVAL;
+    }
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs = new_plan(kProduct, s, N, offset, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    set_reduction(*pl, 1, 256, 2);
+    const size_t es = prec == RQMC_FP32 ? 4 : 8;
+    std::vector<unsigned char> model(2 * es * s);
+    for (int j = 0; j < s; ++j) {
+        const double a = a_host[j], ia = 1.0 / (1.0 + a_host[j]);
+        if (es == 4) {
+            float af = (float)a, iaf = (float)ia;
+            std::memcpy(&model[j * 4], &af, 4);
+            std::memcpy(&model[(s + j) * 4], &iaf, 4);
+        } else {
+            std::memcpy(&model[j * 8], &a, 8);
+            std::memcpy(&model[(s + j) * 8], &ia, 8);
+        }
+    }
+    size_t moff = 0;
+    rs = finish_plan(pl, model, 16, partial_capacity(*pl, 1), 0, &moff);
+    if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
+    unsigned char *d = static_cast<unsigned char *>(pl->d_buf) + moff;
+    if (es == 4) pl->prod32 = ProductModel<float>{s, (const float *)d, (const float *)(d + 4 * s)};
+    else pl->prod64 = ProductModel<double>{s, (const double *)d, (const double *)(d + 8 * s)};
+    pl->launches = 2;
+    *plan = pl;
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_plan_caplets(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes,
+                                         int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
+                                         rqmc_precision prec, rqmc_plan **plan) {
+    rqmc_status rs = check_lmm(p, strikes_host, n_strikes, false);
+    if (rs != RQMC_OK) return rs;
+    rqmc_plan *pl = nullptr;
+    rs = new_plan(kCaplets, p->n_fwd * p->n_factors, N, offset, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    const int nout = p->n_fwd * n_strikes;
+    pl->nf_bucket = lmm_bucket(p->n_fwd);
+    set_reduction(*pl, nout, 256, prec == RQMC_FP32 ? 2 : 1);
+    if (prec == RQMC_FP32) fill_lmm(pl->lmm32, p, strikes_host, n_strikes, pl->nf_bucket);
+    else fill_lmm(pl->lmm64, p, strikes_host, n_strikes, pl->nf_bucket);
+    rs = finish_plan(pl, {}, 16, partial_capacity(*pl, nout), 0, nullptr);
+    if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
+    pl->launches = 2;
+    *plan = pl;
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_plan_mbs(const rqmc_mbs_params *p, int64_t N, int64_t offset, int M, rqmc_sequence seq,
+                                     uint64_t seed, rqmc_precision prec, rqmc_plan **plan) {
+    rqmc_status rs = check_mbs(p);
+    if (rs != RQMC_OK) return rs;
+    rqmc_plan *pl = nullptr;
+    rs = new_plan(kMbs, p->months, N, offset, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    set_reduction(*pl, 1, 256, 1);
+    const int Mm = p->months;
+    const double v = 1.0 / (1.0 + p->i0);
+    std::vector<double> ck(Mm + 1, 0.0);
+    for (int k = 1; k <= Mm; ++k) {   // c_k = sum_{j=0}^{M-k} (1+i0)^-j
+        double acc = 0.0, pw = 1.0;
+        for (int j = 0; j <= Mm - k; ++j) { acc += pw; pw *= v; }
+        ck[k] = acc;
+    }
+    const size_t es = prec == RQMC_FP32 ? 4 : 8;
+    std::vector<unsigned char> model(es * (Mm + 1));
+    for (int k = 0; k <= Mm; ++k) {
+        if (es == 4) { float f = (float)ck[k]; std::memcpy(&model[k * 4], &f, 4); }
+        else std::memcpy(&model[k * 8], &ck[k], 8);
+    }
+    size_t moff = 0;
+    rs = finish_plan(pl, model, 16, partial_capacity(*pl, 1), 0, &moff);
+    if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
+    const unsigned char *d = static_cast<unsigned char *>(pl->d_buf) + moff;
+    const double s2 = p->sigma * p->sigma;
+    if (es == 4) {
+        const double l2e = 1.4426950408889634;
+        pl->mbs32 = MbsModel<float>{Mm, (float)p->i0, (float)p->K1, (float)p->K2, (float)p->K3, (float)p->K4,
+                                    (float)p->c, (float)v, (float)(-0.5 * s2 * l2e), (float)(p->sigma * l2e),
+                                    (const float *)d};
+    } else {
+        pl->mbs64 = MbsModel<double>{Mm, p->i0, p->K1, p->K2, p->K3, p->K4, p->c, v, -0.5 * s2, p->sigma,
+                                     (const double *)d};
+    }
+    pl->launches = 2;
+    *plan = pl;
+    return RQMC_OK;
+}
+
+extern "C" int64_t rqmc_plan_output_size(const rqmc_plan *plan) {
+    if (!plan) return -1;
+    return (int64_t)plan->M * plan->nout;
+}
+
+extern "C" int rqmc_plan_launches(const rqmc_plan *plan) { return plan ? plan->launches : 0; }
+
+extern "C" rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int paths_per_thread) {
+    if (!plan) { set_error("plan is NULL"); return RQMC_EINVAL; }
+    int t = threads > 0 ? threads : plan->threads;
+    int p = paths_per_thread > 0 ? paths_per_thread : plan->ppt;
+    if (t % 32 != 0 || t < 32 || t > 256 || p < 1 || p > 64) {
+        set_error("threads must be a multiple of 32 in 32..256, paths_per_thread in 1..64");
+        return RQMC_EINVAL;
+    }
+    if (plan->kind == kCaplets) {
+        const size_t es = plan->prec == RQMC_FP32 ? 4 : 8;
+        if (2ull * (t / 32) * plan->nout * es > 200 * 1024) { set_error("accumulators exceed shared memory"); return RQMC_EINVAL; }
+    }
+    set_reduction(*plan, plan->nout, t, p);
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, void *stream) {
+    if (!plan || !theta_dev) { set_error("plan and theta_dev are required"); return RQMC_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    switch (plan->kind) {
+        case kProduct: e = launch_product(*plan, st); break;
+        case kCaplets: e = launch_caplets(*plan, st); break;
+        case kMbs: e = launch_mbs(*plan, st); break;
+        default: set_error("plan kind cannot be executed"); return RQMC_EUNSUPPORTED;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "path kernel launch");
+    if ((e = launch_theta(*plan, theta_dev, st)) != cudaSuccess) return cuda_fail(e, "reduction launch");
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_plan_check(rqmc_plan *plan, void *stream) {
+    if (!plan) { set_error("plan is NULL"); return RQMC_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, reinterpret_cast<unsigned char *>(plan->red.status) - sizeof(uint32_t),
+                                    sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    if (h[0]) { set_error("randomized point range exceeds the start digits (offset + N too large)"); return RQMC_EUNSUPPORTED; }
+    if (h[1] == 2) { set_error("device wait timed out"); return RQMC_ETIMEOUT; }
+    if (h[1]) { set_error("device-side check failed"); return RQMC_ECUDA; }
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_plan_destroy(rqmc_plan *plan) {
+    if (!plan) return RQMC_OK;
+    destroy(plan, 0);
+    return RQMC_OK;
+}
+
+// ------------------------------------------------------------------ point stream
+extern "C" rqmc_status rqmc_points(int s, int64_t N, int M, rqmc_sequence seq, uint64_t seed, int64_t offset,
+                                   rqmc_precision prec, rqmc_transform tr, void *out, void *stream) {
+    if (!out) { set_error("out is NULL"); return RQMC_EINVAL; }
+    if (tr < RQMC_UNIFORM || tr > RQMC_RAW) { set_error("unknown transform"); return RQMC_EINVAL; }
+    if ((int64_t)M * s * N > (int64_t(1) << 40)) { set_error("output too large"); return RQMC_EINVAL; }
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs = new_plan(kPoints, s, N, offset, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    rs = finish_plan(pl, {}, 16, 1, st, nullptr);
+    if (rs != RQMC_OK) { destroy(pl, st); return rs; }
+    cudaError_t e = launch_points(*pl, tr, out, st);
+    destroy(pl, st);   // stream-ordered free after the kernel
+    if (e != cudaSuccess) return cuda_fail(e, "points launch");
+    return RQMC_OK;
+}
+
+// ------------------------------------------------------------------ one-shot estimators
+static rqmc_status run_oneshot(rqmc_plan *pl, double *theta_host, double *rq_host, double *sd_host, void *stream) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = rqmc_plan_output_size(pl);
+    double *theta_dev = nullptr;
+    cudaError_t e = cudaMallocAsync(&theta_dev, sizeof(double) * n, st);
+    if (e != cudaSuccess) { destroy(pl, st); set_error("device allocation failed"); return RQMC_ENOMEM; }
+    rqmc_status rs = rqmc_plan_execute(pl, theta_dev, stream);
+    if (rs == RQMC_OK) {
+        e = cudaMemcpyAsync(theta_host, theta_dev, sizeof(double) * n, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rs = cuda_fail(e, "result copy");
+    }
+    if (rs == RQMC_OK) rs = rqmc_plan_check(pl, stream);   // synchronises
+    cudaFreeAsync(theta_dev, st);
+    const int M = pl->M, nout = pl->nout;
+    destroy(pl, st);
+    if (rs != RQMC_OK) return rs;
+    for (int o = 0; o < nout; ++o) {
+        double mean = 0.0;
+        for (int m = 0; m < M; ++m) mean += theta_host[(size_t)m * nout + o];
+        mean /= M;
+        double ss = 0.0;
+        for (int m = 0; m < M; ++m) {
+            const double d = theta_host[(size_t)m * nout + o] - mean;
+            ss += d * d;
+        }
+        if (rq_host) rq_host[o] = mean;
+        if (sd_host) sd_host[o] = M > 1 ? std::sqrt(ss / (M - 1)) : 0.0;
+    }
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_integrate_product(int s, int64_t N, int M, rqmc_sequence seq, uint64_t seed,
+                                              const double *a_host, rqmc_precision prec, double *theta_host,
+                                              double *rq_host, double *sd_host, void *stream) {
+    if (!theta_host) { set_error("theta_host is NULL"); return RQMC_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_oneshot_mu);
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs = rqmc_plan_product(s, N, 0, M, seq, seed, a_host, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    return run_oneshot(pl, theta_host, rq_host, sd_host, stream);
+}
+
+extern "C" rqmc_status price_caplets(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes, int64_t N,
+                                     int M, rqmc_sequence seq, uint64_t seed, rqmc_precision prec, double *theta_host,
+                                     double *rq_host, double *sd_host, void *stream) {
+    if (!theta_host) { set_error("theta_host is NULL"); return RQMC_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_oneshot_mu);
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs = rqmc_plan_caplets(p, strikes_host, n_strikes, N, 0, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    return run_oneshot(pl, theta_host, rq_host, sd_host, stream);
+}
+
+extern "C" rqmc_status price_mbs(const rqmc_mbs_params *p, int64_t N, int M, rqmc_sequence seq, uint64_t seed,
+                                 rqmc_precision prec, double *theta_host, double *rq_host, double *sd_host,
+                                 void *stream) {
+    if (!theta_host) { set_error("theta_host is NULL"); return RQMC_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_oneshot_mu);
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs = rqmc_plan_mbs(p, N, 0, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    return run_oneshot(pl, theta_host, rq_host, sd_host, stream);
+}
+
+// ------------------------------------------------------------------ not yet built in this file
+extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *, const double *, int, const double *, int64_t,
+                                         int64_t, int, rqmc_sequence, uint64_t, rqmc_precision, int, rqmc_plan **) {
+    set_error("adjoint plans are not built yet");
+    return RQMC_EUNSUPPORTED;
+}
+extern "C" rqmc_status price_adjoint(const rqmc_lmm_params *, const double *, int, const double *, int64_t, int,
+                                     rqmc_sequence, uint64_t, rqmc_precision, int, double *, double *, double *,
+                                     void *) {
+    set_error("price_adjoint is not built yet");
+    return RQMC_EUNSUPPORTED;
+}
+extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *, int, int, rqmc_sequence, uint64_t, rqmc_precision,
+                                       rqmc_plan **) {
+    set_error("batch plans are not built yet");
+    return RQMC_EUNSUPPORTED;
+}
+extern "C" rqmc_status price_batch(const rqmc_instrument *, int, int, rqmc_sequence, uint64_t, rqmc_precision,
+                                   double *, void *) {
+    set_error("price_batch is not built yet");
+    return RQMC_EUNSUPPORTED;
+}

@@ -1,0 +1,87 @@
+// k_mbs.cu -- fused mortgage-backed-security kernel (Sec. 6, Caflisch's model).
+//
+// One thread = one path: for month k = 1..M, coordinate k-1 -> Phi^-1 -> xi_k = sigma z_k,
+//   i_k = K0 e^{xi_k} i_{k-1},  w_k = K1 + K2 atan(K3 i_k + K4),
+//   m_k = c r_k ((1 - w_k) + w_k c_k),  v += u_k m_k  (Kahan in FP32),
+//   u_{k+1} = u_k / (1 + i_k),  r_{k+1} = r_k (1 - w_k).
+// The path value v is summed over the warp and accumulated per warp and unit.
+#include "paths_common.cuh"
+
+namespace rqmc {
+
+template <typename T>
+__device__ __forceinline__ T mbs_exp(T x);
+template <>
+__device__ __forceinline__ float mbs_exp<float>(float x) { return ex2_approx(x); }
+template <>
+__device__ __forceinline__ double mbs_exp<double>(double x) { return exp(x); }
+
+__device__ __forceinline__ float mbs_atan(float x) { return atanf(x); }
+__device__ __forceinline__ double mbs_atan(double x) { return atan(x); }
+
+template <typename T>
+__device__ __forceinline__ T mbs_path(PathGen &pg, const MbsModel<T> &md, const T *__restrict__ ck) {
+    T ip = md.i0, u = md.u1, rr = T(1), v = T(0), vc = T(0);
+    for (int k = 1; k <= md.months; ++k) {
+        const T z = NormalOf<T>::get(pg, k - 1);
+        const T ik = ip * mbs_exp<T>(fmaT(md.sz, z, md.lk0));
+        const T w = fmaT(md.K2, mbs_atan(fmaT(md.K3, ik, md.K4)), md.K1);
+        const T mk = md.c * rr * ((T(1) - w) + w * ck[k]);
+        if constexpr (sizeof(T) == 4) kahan_add(v, vc, u * mk);
+        else v += u * mk;
+        u *= fast_rcp<T>(T(1) + ik);
+        rr *= T(1) - w;
+        ip = ik;
+    }
+    return v - vc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsModel<T> md, const RedParams r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *acc = reinterpret_cast<T *>(smem_raw);
+    T *cmp = acc + nw;
+    T *ck = cmp + nw;
+    for (int k = threadIdx.x; k <= md.months; k += blockDim.x) ck[k] = md.ck[k];
+    zero_acc(acc, cmp, nw);
+    __syncthreads();
+    uint32_t u0, u1;
+    unit_range(r, u0, u1);
+    for (uint32_t u = u0; u < u1; ++u) {
+        const int m = (int)(u / r.tiles_per_m);
+        const uint32_t tile = u % r.tiles_per_m;
+        for (int pp = 0; pp < r.ppt; ++pp) {
+            const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
+            const bool active = i < r.N;
+            if (!__any_sync(0xffffffffu, active)) break;
+            PathGen pg;
+            pg.init(g, m, active ? i : 0u);
+            const T v = mbs_path<T>(pg, md, ck);
+            warp_accumulate<T>(active ? v : T(0), acc + warp, cmp + warp, 0, lane);
+        }
+        flush_unit(r, u, acc, cmp);
+    }
+}
+
+template <typename T>
+static cudaError_t launch_mbs_t(const Plan &pl, const MbsModel<T> &md, cudaStream_t st) {
+    auto kern = mbs_kernel<T>;
+    const int threads = pl.threads;
+    const size_t smem = (2ull * (threads / 32) + md.months + 1) * sizeof(T);
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (occ < 1) occ = 1;
+    unsigned grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)occ * sms);
+    if (pl.grid > 0) grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)pl.grid);
+    kern<<<grid, threads, smem, st>>>(pl.gen, md, pl.red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mbs(const Plan &pl, cudaStream_t st) {
+    return pl.prec == RQMC_FP32 ? launch_mbs_t(pl, pl.mbs32, st) : launch_mbs_t(pl, pl.mbs64, st);
+}
+
+}  // namespace rqmc

@@ -1,0 +1,77 @@
+// k_product.cu -- product test integrand f(x) = prod_j (|4 x_j - 2| + a_j)/(1 + a_j) and the
+// final replication reduction theta_N^m = (1/N) sum_i f(q_i^m) (Sec. 1).
+#include "paths_common.cuh"
+
+namespace rqmc {
+
+template <typename T>
+__global__ void __launch_bounds__(256) product_kernel(const GenParams g, const ProductModel<T> md,
+                                                      const RedParams r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *acc = reinterpret_cast<T *>(smem_raw);
+    T *cmp = acc + nw;
+    zero_acc(acc, cmp, nw);
+    __syncthreads();
+    uint32_t u0, u1;
+    unit_range(r, u0, u1);
+    for (uint32_t u = u0; u < u1; ++u) {
+        const int m = (int)(u / r.tiles_per_m);
+        const uint32_t tile = u % r.tiles_per_m;
+        for (int pp = 0; pp < r.ppt; ++pp) {
+            const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
+            const bool active = i < r.N;
+            if (!__any_sync(0xffffffffu, active)) break;
+            PathGen pg;
+            pg.init(g, m, active ? i : 0u);
+            T f = T(1);
+            for (int j = 0; j < md.s; ++j) {
+                const T x = UniformOf<T>::get(pg, j);
+                f *= (fabs(T(4) * x - T(2)) + md.a[j]) * md.inv1pa[j];
+            }
+            warp_accumulate<T>(active ? f : T(0), acc + warp, cmp + warp, 0, lane);
+        }
+        flush_unit(r, u, acc, cmp);
+    }
+}
+
+template <typename T>
+static cudaError_t launch_product_t(const Plan &pl, const ProductModel<T> &md, cudaStream_t st) {
+    auto kern = product_kernel<T>;
+    const int threads = pl.threads;
+    const size_t smem = 2ull * (threads / 32) * sizeof(T);
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (occ < 1) occ = 1;
+    unsigned grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)occ * sms);
+    if (pl.grid > 0) grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)pl.grid);
+    kern<<<grid, threads, smem, st>>>(pl.gen, md, pl.red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_product(const Plan &pl, cudaStream_t st) {
+    return pl.prec == RQMC_FP32 ? launch_product_t(pl, pl.prod32, st) : launch_product_t(pl, pl.prod64, st);
+}
+
+// theta[m][o] = (sum over the tiles of replication m, in tile order) / N
+__global__ void theta_kernel(const double *__restrict__ partials, int nout, uint32_t tiles_per_m, int M, double N,
+                             double *__restrict__ theta) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * nout) return;
+    const int m = idx / nout, o = idx % nout;
+    const double *p = partials + (size_t)m * tiles_per_m * nout + o;
+    double s = 0.0;
+    for (uint32_t t = 0; t < tiles_per_m; ++t) s += p[(size_t)t * nout];
+    theta[idx] = s / N;
+}
+
+cudaError_t launch_theta(const Plan &pl, double *theta_dev, cudaStream_t st) {
+    const int n = pl.M * pl.red.nout;
+    theta_kernel<<<(n + 255) / 256, 256, 0, st>>>(pl.red.partials, pl.red.nout, pl.red.tiles_per_m, pl.M,
+                                                   (double)pl.N, theta_dev);
+    return cudaGetLastError();
+}
+
+}  // namespace rqmc

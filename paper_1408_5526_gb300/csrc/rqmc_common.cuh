@@ -1,0 +1,315 @@
+// rqmc_common.cuh -- device building blocks of the RQMC hot path (sm_103a).
+//
+//   * Philox4x32-10 (Salmon et al., SC'11), the Sec. 2 counter-based stream and
+//     the source of every randomization
+//   * counter-based random-start permuted van der Corput (Sec. 3.1, Algorithm 3,
+//     eq. perm) in exact integer digit arithmetic
+//   * Sobol' in binary counter order with a digital shift (Sec. 3.2)
+//   * the inverse normal CDF (our own fit, Giles' polynomial form) in FP32, and
+//     in FP64 with one Halley correction on erfc
+//   * warp-shuffle reductions
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ndtri_coeffs.h"
+
+namespace rqmc {
+
+constexpr int kMaxStrikes = 8;
+
+// ------------------------------------------------------------------ SFU wrappers (PTX ISA)
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+struct U32x4 {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+// Ten rounds; each round multiplies words 0 and 2 by 0xD2511F53 / 0xCD9E8D57,
+// mixes the high halves into words 1 and 3 with the key, and bumps the key by
+// the Weyl constants 0x9E3779B9 / 0xBB67AE85.
+__host__ __device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                        uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = mulhi32(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = mulhi32(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return U32x4{c0, c1, c2, c3};
+}
+
+// Counter tags (low byte of counter word 3; the instrument index sits above it).
+enum : uint32_t { kTagPath = 0, kTagStart = 1, kTagPerm = 2, kTagShift = 3 };
+
+// ------------------------------------------------------------------ sequence descriptors
+enum Seq : int { kHaltonRS = 0, kRasrap = 1, kSobolDS = 2, kPhilox = 3 };
+
+// Per (replication m, dimension j) description of the random-start permuted van der
+// Corput points phi_p^sigma(n0 + offset + i), i < N, split at digit L:
+//   low  = lo0 + i                      (lo0 = (n0+offset) mod p^L, carry c = low >= p^L)
+//   R    = sum_{k<L} sigma(d_k) p^(L-1-k) over the digits d_k of low mod p^L
+//   num  = R * P + S[c]                 (P = p^(K+1-L); S[c] = the permuted high digits
+//                                        of (n0+offset) div p^L + c at positions L..K)
+// num / p^(K+1) is exactly the point of eq. (perm) with all K start positions permuted.
+struct __align__(16) HaltonDim {
+    unsigned long long P;
+    unsigned long long S[2];
+    double invD;             // 1 / p^(K+1) (FP64 conversion)
+    uint32_t p, L, pL, lo0;
+    uint32_t magic;          // floor(2^32 / p) + 1: q = umulhi(x, magic) is floor(x/p) or one more
+    uint32_t sig_off;        // offset of sigma_{m,j} inside replication m's permutation table
+    float inv_pL;            // FP32 conversion: u = R / p^L + (S[c] + 1/2) / D
+    float a[2];              // (S[c] + 1/2) / D
+    float b[2];              // (P - 1 - S[c] + 1/2) / D, the complement's tail
+    float pad_;
+};
+
+struct GenParams {
+    int seq;
+    int s;
+    int M;
+    uint32_t key0, key1;
+    uint32_t inst;           // instrument index (batched launches)
+    unsigned long long offset;
+    const HaltonDim *hdim;   // [M][s]
+    const uint16_t *sigma;   // [M][sig_len]
+    unsigned long long sig_len;
+    const uint32_t *sobV;    // [s][32]
+    const uint32_t *sobShift;// [M][s]
+    int sob_bits;            // bits of offset + N - 1
+};
+
+// ------------------------------------------------------------------ Halton digits
+// Digits of low = lo0 + i in base p, each mapped through sigma and accumulated in
+// Horner order (sigma(d_0) most significant).  Exact; no divergence (L is uniform).
+__device__ __forceinline__ uint32_t halton_R(const HaltonDim &h, const uint16_t *__restrict__ sig, uint32_t i,
+                                             uint32_t &carry) {
+    uint32_t low = h.lo0 + i;
+    carry = low >= h.pL ? 1u : 0u;
+    low -= carry ? h.pL : 0u;
+    uint32_t r = 0;
+    const uint16_t *sg = sig + h.sig_off;
+    for (uint32_t k = 0; k < h.L; ++k) {
+        uint32_t q = __umulhi(low, h.magic);
+        uint32_t d = low - q * h.p;
+        if ((int32_t)d < 0) {   // the rounded-up reciprocal overshot by one
+            d += h.p;
+            q -= 1;
+        }
+        r = r * h.p + (uint32_t)__ldg(sg + d);
+        low = q;
+    }
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long halton_num(const HaltonDim &h, uint32_t R, uint32_t c) {
+    return (unsigned long long)R * h.P + h.S[c];
+}
+
+// u <= 1/2 side test, exact: num <= D-1-num.
+__device__ __forceinline__ bool halton_lower(const HaltonDim &h, uint32_t R, uint32_t c) {
+    const uint32_t Rc = h.pL - 1u - R;
+    if (R != Rc) return R < Rc;
+    const unsigned long long S = h.S[c];
+    return S <= h.P - 1ull - S;
+}
+
+// ------------------------------------------------------------------ Sobol'
+__device__ __forceinline__ uint32_t sobol_x(const uint32_t *__restrict__ V, uint32_t shift, uint32_t n, int nbits) {
+    uint32_t x = shift;
+#pragma unroll 4
+    for (int k = 0; k < nbits; ++k)
+        if ((n >> k) & 1u) x ^= __ldg(V + k);
+    return x;
+}
+
+// ------------------------------------------------------------------ uniforms
+// Every coordinate is delivered as (q, lower): q = (min(num, D-1-num) + 1/2)/D and
+// lower = (num <= D-1-num).  u = lower ? q : 1 - q.
+struct Unif32 {
+    float q;
+    bool lower;
+};
+struct Unif64 {
+    double q;
+    bool lower;
+};
+
+__device__ __forceinline__ Unif32 unif32_from_u32(uint32_t x) {
+    const bool lower = x < 0x80000000u;
+    const uint32_t qx = lower ? x : ~x;
+    return Unif32{fmaf((float)qx, 2.3283064365386963e-10f, 1.1641532182693481e-10f), lower};
+}
+__device__ __forceinline__ Unif64 unif64_from_u32(uint32_t x) {
+    const bool lower = x < 0x80000000u;
+    const uint32_t qx = lower ? x : ~x;
+    return Unif64{((double)qx + 0.5) * 2.3283064365386963e-10, lower};
+}
+__device__ __forceinline__ Unif32 unif32_halton(const HaltonDim &h, uint32_t R, uint32_t c) {
+    const bool lower = halton_lower(h, R, c);
+    const float q = lower ? fmaf((float)R, h.inv_pL, h.a[c]) : fmaf((float)(h.pL - 1u - R), h.inv_pL, h.b[c]);
+    return Unif32{q, lower};
+}
+__device__ __forceinline__ Unif64 unif64_halton(const HaltonDim &h, uint32_t R, uint32_t c) {
+    const unsigned long long num = halton_num(h, R, c);
+    const unsigned long long D1 = (unsigned long long)h.pL * h.P - 1ull;   // D - 1
+    const bool lower = num <= D1 - num;
+    const unsigned long long qn = lower ? num : D1 - num;
+    return Unif64{((double)qn + 0.5) * h.invD, lower};
+}
+
+// Stateful per-thread coordinate source for one path (fixed m and point i).
+// Philox words come four dimensions at a time and are cached.
+struct PathGen {
+    const GenParams *g;
+    int m;
+    uint32_t i;
+    unsigned long long n;   // offset + i
+    int blk;
+    U32x4 words;
+
+    __device__ __forceinline__ void init(const GenParams &gp, int m_, uint32_t i_) {
+        g = &gp;
+        m = m_;
+        i = i_;
+        n = gp.offset + i_;
+        blk = -1;
+    }
+    __device__ __forceinline__ uint32_t philox_word(int j) {
+        if ((j >> 2) != blk) {
+            blk = j >> 2;
+            words = philox4x32_10((uint32_t)n, (uint32_t)((n >> 32) & 0xFFFFu) | ((uint32_t)blk << 16),
+                                  (uint32_t)m, kTagPath | (g->inst << 8), g->key0, g->key1);
+        }
+        const int w = j & 3;
+        return w == 0 ? words.x : w == 1 ? words.y : w == 2 ? words.z : words.w;
+    }
+    __device__ __forceinline__ Unif32 unif32(int j) {
+        const int seq = g->seq;
+        if (seq == kPhilox) return unif32_from_u32(philox_word(j));
+        if (seq == kSobolDS)
+            return unif32_from_u32(sobol_x(g->sobV + 32 * j, __ldg(g->sobShift + (size_t)m * g->s + j), (uint32_t)n,
+                                           g->sob_bits));
+        const HaltonDim &h = g->hdim[(size_t)m * g->s + j];
+        uint32_t c;
+        const uint32_t R = halton_R(h, g->sigma + (size_t)m * g->sig_len, i, c);
+        return unif32_halton(h, R, c);
+    }
+    __device__ __forceinline__ Unif64 unif64(int j) {
+        const int seq = g->seq;
+        if (seq == kPhilox) return unif64_from_u32(philox_word(j));
+        if (seq == kSobolDS)
+            return unif64_from_u32(sobol_x(g->sobV + 32 * j, __ldg(g->sobShift + (size_t)m * g->s + j), (uint32_t)n,
+                                           g->sob_bits));
+        const HaltonDim &h = g->hdim[(size_t)m * g->s + j];
+        uint32_t c;
+        const uint32_t R = halton_R(h, g->sigma + (size_t)m * g->sig_len, i, c);
+        return unif64_halton(h, R, c);
+    }
+};
+
+// ------------------------------------------------------------------ inverse normal CDF
+// erfinv(y)/y as a polynomial in w = -ln(4q(1-q)) (three branches, coefficients
+// fitted by fit_ndtri.py); Phi^-1(u) = -/+ sqrt(2) y P(w), y = 1 - 2q.
+template <typename T, int N>
+__device__ __forceinline__ T horner(const T (&c)[N], T x) {
+    T p = c[N - 1];
+#pragma unroll
+    for (int k = N - 2; k >= 0; --k) p = p * x + c[k];
+    return p;
+}
+
+__device__ __forceinline__ float erfinv_ratio32(float w) {
+    constexpr float C[] = RQMC_NDTRI_C;
+    constexpr float T[] = RQMC_NDTRI_T;
+    constexpr float U[] = RQMC_NDTRI_U;
+    if (w < (float)RQMC_NDTRI_W_SPLIT) return horner(C, w - (float)RQMC_NDTRI_W_MID);
+    const float sw = sqrt_approx(w);
+    if (w < (float)RQMC_NDTRI_W_SPLIT2) return horner(T, sw - (float)RQMC_NDTRI_T_MID);
+    return horner(U, sw - (float)RQMC_NDTRI_U_MID);
+}
+
+__device__ __forceinline__ float ndtri32(Unif32 v) {
+    const float q = v.q;
+    const float t = 4.0f * q * (1.0f - q);
+    const float w = -0.6931471805599453f * lg2_approx(t);
+    const float y = fmaf(-2.0f, q, 1.0f);
+    const float x = 1.4142135623730951f * y * erfinv_ratio32(w);
+    return v.lower ? -x : x;
+}
+
+__device__ __forceinline__ double erfinv_ratio64(double w) {
+    constexpr double C[] = RQMC_NDTRI_C;
+    constexpr double T[] = RQMC_NDTRI_T;
+    constexpr double U[] = RQMC_NDTRI_U;
+    if (w < RQMC_NDTRI_W_SPLIT) return horner(C, w - RQMC_NDTRI_W_MID);
+    const double sw = sqrt(w);
+    if (w < RQMC_NDTRI_W_SPLIT2) return horner(T, sw - RQMC_NDTRI_T_MID);
+    return horner(U, sw - RQMC_NDTRI_U_MID);
+}
+
+// FP64: polynomial start (~1e-7 relative), then one Halley step on
+// F(x) = erfc(-x/sqrt 2)/2 - q, which brings x to full double precision.
+__device__ __forceinline__ double ndtri64(Unif64 v) {
+    const double q = v.q;
+    const double w = -log(4.0 * q * (1.0 - q));
+    const double y = 1.0 - 2.0 * q;
+    double x = -1.4142135623730951 * y * erfinv_ratio64(w);   // Phi^-1(q) <= 0
+    if (q < 0.5) {
+        const double F = 0.5 * erfc(-x * 0.7071067811865476) - q;
+        const double dens = 0.3989422804014327 * exp(-0.5 * x * x);
+        const double t = F / dens;
+        x = x - t / (1.0 + 0.5 * x * t);
+    }
+    return v.lower ? x : -x;
+}
+
+// ------------------------------------------------------------------ reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &sum, T &comp, T x) {
+    const T y = x - comp;
+    const T t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+}  // namespace rqmc

@@ -1,0 +1,140 @@
+// rqmc_internal.h -- library-internal plan layout and kernel launchers.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/rqmc.h"
+#include "rqmc_common.cuh"
+
+namespace rqmc {
+
+constexpr int kMaxFwd = 160;       // forwards per LMM instrument (register-resident buckets 16/40/80/160)
+constexpr int kMaxDims = 4096;
+constexpr int kMaxOutputs = 1280;  // nf * n_strikes per caplet plan
+
+// Reduction layout: a unit is (replication m, tile of `tile` consecutive paths);
+// each unit writes its own row of `nout` doubles, so the result does not depend on
+// which CTA processed it.  theta[m][o] = sum_tiles partial / N in tile order.
+struct RedParams {
+    int nout;
+    int ppt;                 // paths per thread per unit
+    uint32_t tile;           // threads * ppt
+    uint32_t tiles_per_m;
+    uint32_t units;          // M * tiles_per_m
+    uint32_t N;
+    double *partials;        // [units][nout]
+    uint32_t *status;        // device status word (0 = ok)
+};
+
+template <typename T>
+struct LmmModel {
+    int nf, nK;
+    T dl;                    // delta
+    T disc0;                 // 1 / (1 + delta L_0(0))
+    T K[kMaxStrikes];
+    T L0[kMaxFwd];           // L_1(0) .. L_nf(0)
+    T sg[kMaxFwd];           // sigma_n (one factor)
+    T cdr[kMaxFwd];          // drift coefficient sigma_n h        (FP32: times log2 e)
+    T cc[kMaxFwd];           // -sigma_n^2 h / 2                    (FP32: times log2 e)
+    T cz[kMaxFwd];           // sigma_n sqrt(h)                     (FP32: times log2 e)
+};
+
+template <typename T>
+struct MbsModel {
+    int months;
+    T i0, K1, K2, K3, K4, c;
+    T u1;                    // u_1 = 1 / (1 + i_0)
+    T lk0;                   // log K0 = -sigma^2/2        (FP32: log2 K0)
+    T sz;                    // sigma                      (FP32: sigma log2 e)
+    const T *ck;             // [months + 1] remaining-annuity factors c_k (device)
+};
+
+template <typename T>
+struct ProductModel {
+    int s;
+    const T *a;              // [s] (device)
+    const T *inv1pa;         // [s] 1/(1+a_j) (device)
+};
+
+// Per-base constants computed on the host; the device setup kernel completes the
+// per-(m, j) HaltonDim from the Philox draws.
+struct BaseConst {
+    uint32_t p, K, L, pL;
+    unsigned long long P, D, pK;
+    uint32_t magic, sig_off;
+    float inv_pL;
+    double invD;
+};
+
+enum PlanKind { kPoints = 0, kProduct = 1, kCaplets = 2, kMbs = 3, kAdjoint = 4, kBatch = 5 };
+
+struct BatchPlan;
+
+struct Plan {
+    PlanKind kind;
+    int prec;                // RQMC_FP64 / RQMC_FP32
+    int seq;
+    int s, M;
+    uint64_t N, offset, seed;
+    uint32_t inst;
+    int nout;
+    GenParams gen{};
+    RedParams red{};
+    int threads = 256, ppt = 4, grid = 0;
+    int nf_bucket = 0;
+    int launches = 0;
+    // device memory (one allocation)
+    void *d_buf = nullptr;
+    size_t d_bytes = 0;
+    // models
+    LmmModel<float> lmm32{};
+    LmmModel<double> lmm64{};
+    MbsModel<float> mbs32{};
+    MbsModel<double> mbs64{};
+    ProductModel<float> prod32{};
+    ProductModel<double> prod64{};
+    // adjoint
+    int checkpoint = 0;
+    void *adj = nullptr;
+    BatchPlan *batch = nullptr;
+    int device = 0;
+};
+
+// ---- device memory carve-up helper
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes, size_t align = 256) {
+        off = (off + align - 1) / align * align;
+        size_t r = off;
+        off += bytes;
+        return r;
+    }
+};
+
+// ---- setup (setup.cu)
+struct GenLayout {
+    size_t hdim_off = 0, sigma_off = 0, base_off = 0, sobV_off = 0, shift_off = 0;
+    unsigned long long sig_len = 0;
+    std::vector<BaseConst> bases;
+};
+rqmc_status generator_layout(Plan &pl, Carve &cv, GenLayout &gl);
+rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint32_t *d_status, cudaStream_t st);
+std::vector<uint32_t> first_primes(int s);
+bool sobol_table_ready(int s);
+const std::vector<uint32_t> &sobol_directions();
+
+// ---- launchers (k_*.cu); all asynchronous on `st`
+cudaError_t launch_points(const Plan &pl, int tr, void *out, cudaStream_t st);
+cudaError_t launch_product(const Plan &pl, cudaStream_t st);
+cudaError_t launch_caplets(const Plan &pl, cudaStream_t st);
+cudaError_t launch_mbs(const Plan &pl, cudaStream_t st);
+cudaError_t launch_theta(const Plan &pl, double *theta_dev, cudaStream_t st);
+int occupancy_blocks(const Plan &pl);
+
+// ---- errors
+void set_error(const std::string &msg);
+
+}  // namespace rqmc

@@ -1,0 +1,271 @@
+"""Thin ctypes binding of librqmc.so (include/rqmc.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch supplies device memory and the current CUDA stream.
+The library must have been built (``__graft_entry__.build()`` or
+``python paper_1408_5526_gb300/_build.py``); there is no CPU fallback and a
+missing library raises ``RuntimeError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librqmc.so")
+
+HALTON_RS, RASRAP, SOBOL_DS, PHILOX = 0, 1, 2, 3
+FP64, FP32 = 0, 1
+UNIFORM, NORMAL, RAW = 0, 1, 2
+_SEQ = {"halton_rs": HALTON_RS, "rasrap": RASRAP, "sobol_ds": SOBOL_DS, "philox": PHILOX}
+_PREC = {"fp64": FP64, "fp32": FP32}
+_TR = {"uniform": UNIFORM, "normal": NORMAL, "raw": RAW}
+STATUS = {0: "RQMC_OK", 1: "RQMC_EINVAL", 2: "RQMC_ENOMEM", 3: "RQMC_ECUDA", 4: "RQMC_ETIMEOUT",
+          5: "RQMC_EUNSUPPORTED", 6: "RQMC_ENOTABLE"}
+
+# every symbol include/rqmc.h declares
+EXPORTS = ["rqmc_set_sobol_table", "rqmc_points", "rqmc_integrate_product", "price_caplets", "price_mbs",
+           "price_adjoint", "price_batch", "rqmc_plan_product", "rqmc_plan_caplets", "rqmc_plan_mbs",
+           "rqmc_plan_adjoint", "rqmc_plan_batch", "rqmc_plan_output_size", "rqmc_plan_launches",
+           "rqmc_plan_set_launch", "rqmc_plan_execute", "rqmc_plan_check", "rqmc_plan_destroy",
+           "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version"]
+
+
+class RqmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LmmParams(C.Structure):
+    _fields_ = [("n_fwd", C.c_int), ("n_factors", C.c_int), ("scheme", C.c_int), ("reserved", C.c_int),
+                ("delta", C.c_double), ("L0", C.POINTER(C.c_double)), ("vol", C.POINTER(C.c_double)),
+                ("loadings", C.POINTER(C.c_double))]
+
+
+class MbsParams(C.Structure):
+    _fields_ = [("months", C.c_int), ("reserved", C.c_int), ("i0", C.c_double), ("K1", C.c_double),
+                ("K2", C.c_double), ("K3", C.c_double), ("K4", C.c_double), ("sigma", C.c_double),
+                ("c", C.c_double)]
+
+
+class Instrument(C.Structure):
+    _fields_ = [("kind", C.c_int), ("size", C.c_int), ("N", C.c_int64), ("rate", C.c_double),
+                ("vol", C.c_double), ("strike", C.c_double), ("mbs", MbsParams)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load librqmc.so and hand it the Joe-Kuo Sobol' table; raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"librqmc.so not built ({path}); run __graft_entry__.build() -- no CPU fallback")
+        L = C.CDLL(path)
+        vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+        st = C.c_int
+        L.rqmc_set_sobol_table.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int, C.c_int]
+        L.rqmc_points.argtypes = [C.c_int, i64, C.c_int, C.c_int, C.c_uint64, i64, C.c_int, C.c_int, vp, vp]
+        L.rqmc_integrate_product.argtypes = [C.c_int, i64, C.c_int, C.c_int, C.c_uint64, dp, C.c_int, dp, dp, dp, vp]
+        L.price_caplets.argtypes = [C.POINTER(LmmParams), dp, C.c_int, i64, C.c_int, C.c_int, C.c_uint64, C.c_int,
+                                    dp, dp, dp, vp]
+        L.price_mbs.argtypes = [C.POINTER(MbsParams), i64, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, dp, dp, vp]
+        L.price_adjoint.argtypes = [C.POINTER(LmmParams), dp, C.c_int, dp, i64, C.c_int, C.c_int, C.c_uint64,
+                                    C.c_int, C.c_int, dp, dp, dp, vp]
+        L.price_batch.argtypes = [C.POINTER(Instrument), C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, vp]
+        pp = C.POINTER(vp)
+        L.rqmc_plan_product.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int, C.c_uint64, dp, C.c_int, pp]
+        L.rqmc_plan_caplets.argtypes = [C.POINTER(LmmParams), dp, C.c_int, i64, i64, C.c_int, C.c_int, C.c_uint64,
+                                        C.c_int, pp]
+        L.rqmc_plan_mbs.argtypes = [C.POINTER(MbsParams), i64, i64, C.c_int, C.c_int, C.c_uint64, C.c_int, pp]
+        L.rqmc_plan_adjoint.argtypes = [C.POINTER(LmmParams), dp, C.c_int, dp, i64, i64, C.c_int, C.c_int,
+                                        C.c_uint64, C.c_int, C.c_int, pp]
+        L.rqmc_plan_batch.argtypes = [C.POINTER(Instrument), C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, pp]
+        L.rqmc_plan_output_size.argtypes = [vp]
+        L.rqmc_plan_output_size.restype = i64
+        L.rqmc_plan_launches.argtypes = [vp]
+        L.rqmc_plan_set_launch.argtypes = [vp, C.c_int, C.c_int]
+        L.rqmc_plan_execute.argtypes = [vp, dp, vp]
+        L.rqmc_plan_check.argtypes = [vp, vp]
+        L.rqmc_plan_destroy.argtypes = [vp]
+        L.rqmc_status_string.argtypes = [st]
+        L.rqmc_status_string.restype = C.c_char_p
+        L.rqmc_last_error.restype = C.c_char_p
+        for name in EXPORTS:
+            getattr(L, name)
+        poly, vinit = inputs.joe_kuo_table()
+        n = min(len(poly), 4096)
+        _check(L, L.rqmc_set_sobol_table(poly.ctypes.data_as(C.POINTER(C.c_int64)),
+                                         vinit.ctypes.data_as(C.POINTER(C.c_int64)), n, vinit.shape[1]))
+        _lib = L
+        return L
+
+
+def _check(L, status):
+    if status != 0:
+        raise RqmcError(status, L.rqmc_last_error().decode())
+
+
+def _enum(v, table):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _lmm_struct(lmm: dict, keep: list) -> LmmParams:
+    L0 = np.ascontiguousarray(lmm["L0"], dtype=np.float64)
+    vol = np.ascontiguousarray(lmm["vol"], dtype=np.float64)
+    keep += [L0, vol]
+    st = LmmParams(int(lmm["n_fwd"]), int(lmm.get("d", 1)), int(lmm.get("scheme", 0)), 0, float(lmm["delta"]),
+                   _dp(L0), _dp(vol), None)
+    if lmm.get("loadings") is not None:
+        ld = np.ascontiguousarray(lmm["loadings"], dtype=np.float64)
+        keep.append(ld)
+        st.loadings = _dp(ld)
+    return st
+
+
+def _mbs_struct(mbs: dict) -> MbsParams:
+    return MbsParams(int(mbs["months"]), 0, float(mbs["i0"]), float(mbs["K1"]), float(mbs["K2"]),
+                     float(mbs["K3"]), float(mbs["K4"]), float(mbs["sigma"]), float(mbs.get("c", 1.0)))
+
+
+# ------------------------------------------------------------------ point stream
+def rqmc_points(s, N, M, seq, seed, offset=0, prec="fp32", transform="uniform", out=None, stream=None):
+    """Coordinates [M, s, N] on the current CUDA device (torch tensor)."""
+    import torch
+    L = load()
+    tr = _enum(transform, _TR)
+    pr = _enum(prec, _PREC)
+    dt = torch.int64 if tr == RAW else (torch.float32 if pr == FP32 else torch.float64)
+    if out is None:
+        out = torch.empty((M, s, N), dtype=dt, device="cuda")
+    _check(L, L.rqmc_points(s, N, M, _enum(seq, _SEQ), seed, offset, pr, tr, C.c_void_p(out.data_ptr()),
+                            _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------------ one-shot estimators
+def _stats_out(M, nout):
+    return np.zeros((M, nout)), np.zeros(nout), np.zeros(nout)
+
+
+def rqmc_integrate_product(s, N, M, seq, seed, a, prec="fp64", stream=None):
+    L = load()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    th, rq, sd = _stats_out(M, 1)
+    _check(L, L.rqmc_integrate_product(s, N, M, _enum(seq, _SEQ), seed, _dp(a), _enum(prec, _PREC), _dp(th),
+                                       _dp(rq), _dp(sd), _stream(stream)))
+    return th[:, 0], rq[0], sd[0]
+
+
+def price_caplets(lmm: dict, strikes, N, M, seq, seed, prec="fp32", stream=None):
+    """theta [M, n_fwd*n_strikes], RQ and sd over m per caplet/strike."""
+    L = load()
+    keep: list = []
+    p = _lmm_struct(lmm, keep)
+    K = np.ascontiguousarray(strikes, dtype=np.float64)
+    nout = p.n_fwd * len(K)
+    th, rq, sd = _stats_out(M, nout)
+    _check(L, L.price_caplets(C.byref(p), _dp(K), len(K), N, M, _enum(seq, _SEQ), seed, _enum(prec, _PREC),
+                              _dp(th), _dp(rq), _dp(sd), _stream(stream)))
+    return th, rq, sd
+
+
+def price_mbs(mbs: dict, N, M, seq, seed, prec="fp32", stream=None):
+    L = load()
+    p = _mbs_struct(mbs)
+    th, rq, sd = _stats_out(M, 1)
+    _check(L, L.price_mbs(C.byref(p), N, M, _enum(seq, _SEQ), seed, _enum(prec, _PREC), _dp(th), _dp(rq), _dp(sd),
+                          _stream(stream)))
+    return th[:, 0], rq[0], sd[0]
+
+
+# ------------------------------------------------------------------ plans
+class Plan:
+    """Device-resident plan: tables built once, `execute` launches kernels only."""
+
+    def __init__(self, handle, M, nout):
+        self._h = handle
+        self.M = M
+        self.nout = nout
+
+    @classmethod
+    def product(cls, s, N, M, seq, seed, a, prec="fp64", offset=0):
+        L = load()
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        h = C.c_void_p()
+        _check(L, L.rqmc_plan_product(s, N, offset, M, _enum(seq, _SEQ), seed, _dp(a), _enum(prec, _PREC),
+                                      C.byref(h)))
+        return cls(h, M, 1)
+
+    @classmethod
+    def caplets(cls, lmm, strikes, N, M, seq, seed, prec="fp32", offset=0):
+        L = load()
+        keep: list = []
+        p = _lmm_struct(lmm, keep)
+        K = np.ascontiguousarray(strikes, dtype=np.float64)
+        h = C.c_void_p()
+        _check(L, L.rqmc_plan_caplets(C.byref(p), _dp(K), len(K), N, offset, M, _enum(seq, _SEQ), seed,
+                                      _enum(prec, _PREC), C.byref(h)))
+        return cls(h, M, p.n_fwd * len(K))
+
+    @classmethod
+    def mbs(cls, mbs, N, M, seq, seed, prec="fp32", offset=0):
+        L = load()
+        p = _mbs_struct(mbs)
+        h = C.c_void_p()
+        _check(L, L.rqmc_plan_mbs(C.byref(p), N, offset, M, _enum(seq, _SEQ), seed, _enum(prec, _PREC),
+                                  C.byref(h)))
+        return cls(h, M, 1)
+
+    def output_size(self):
+        return int(load().rqmc_plan_output_size(self._h))
+
+    def launches(self):
+        return int(load().rqmc_plan_launches(self._h))
+
+    def set_launch(self, threads=0, paths_per_thread=0):
+        _check(load(), load().rqmc_plan_set_launch(self._h, threads, paths_per_thread))
+
+    def execute(self, theta=None, stream=None):
+        import torch
+        if theta is None:
+            theta = torch.empty(self.output_size(), dtype=torch.float64, device="cuda")
+        L = load()
+        _check(L, L.rqmc_plan_execute(self._h, C.cast(C.c_void_p(theta.data_ptr()), C.POINTER(C.c_double)),
+                                      _stream(stream)))
+        return theta
+
+    def check(self, stream=None):
+        _check(load(), load().rqmc_plan_check(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            load().rqmc_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

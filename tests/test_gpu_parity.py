@@ -1,0 +1,183 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Integer states bit-exact; theta_N^m within the tolerance
+|d| <= 1e-4 max(|theta_oracle|, theta_scale) (theta_scale = the at-the-money
+caplet of the same maturity), FP64 paths far tighter."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1408_5526_gb300 import inputs
+
+JK = inputs.joe_kuo_table()
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def R():
+    from paper_1408_5526_gb300 import _build, rqmc
+    _build.build()
+    rqmc.load()
+    return rqmc
+
+
+def _to_np(t):
+    import torch
+    if t.dtype == torch.int64:
+        return t.cpu().numpy().view(np.uint64)
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------------ point stream
+@pytest.mark.parametrize("seq,s", [(O.HALTON_RS, 8), (O.RASRAP, 8), (O.RASRAP, 360), (O.SOBOL_DS, 40),
+                                   (O.SOBOL_DS, 360), (O.PHILOX, 10)])
+@pytest.mark.parametrize("offset", [0, 12345])
+def test_points_raw_bit_exact(R, seq, s, offset):
+    N, M = 3001, 3
+    gpu = _to_np(R.rqmc_points(s, N, M, seq, 7, offset=offset, transform="raw"))
+    ora = O.Sequence(seq, s, M, 7, joe_kuo=JK).points(N, offset, transform=O.RAW)
+    assert gpu.shape == ora.shape
+    assert np.array_equal(gpu, ora)
+
+
+@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX])
+def test_points_fp64_uniform_and_normal(R, seq):
+    N, M, s = 2500, 2, 16
+    q = O.Sequence(seq, s, M, 11, joe_kuo=JK)
+    u = _to_np(R.rqmc_points(s, N, M, seq, 11, prec="fp64", transform="uniform"))
+    np.testing.assert_allclose(u, q.points(N, transform=O.UNIFORM), rtol=0, atol=4e-16)
+    z = _to_np(R.rqmc_points(s, N, M, seq, 11, prec="fp64", transform="normal"))
+    zo = q.points(N, transform=O.NORMAL)
+    np.testing.assert_allclose(z, zo, rtol=0, atol=2e-14 * np.maximum(1, np.abs(zo)).max())
+
+
+@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX])
+def test_points_fp32_uniform_and_normal(R, seq):
+    N, M, s = 2500, 2, 40
+    q = O.Sequence(seq, s, M, 13, joe_kuo=JK)
+    u = _to_np(R.rqmc_points(s, N, M, seq, 13, prec="fp32", transform="uniform"))
+    uo = q.points(N, transform=O.UNIFORM)
+    np.testing.assert_allclose(u, uo, rtol=4e-7, atol=1e-30)
+    z = _to_np(R.rqmc_points(s, N, M, seq, 13, prec="fp32", transform="normal")).astype(np.float64)
+    zo = q.points(N, transform=O.NORMAL)
+    assert np.max(np.abs(z - zo) / np.maximum(1.0, np.abs(zo))) < 1e-6
+
+
+def test_points_halton_tail_normals_fp32(R):
+    # Halton numerators reach q ~ 1e-19: the FP32 normal keeps its relative accuracy there
+    N, M, s = 4096, 4, 8
+    q = O.Sequence(O.RASRAP, s, M, 5)
+    z = _to_np(R.rqmc_points(s, N, M, O.RASRAP, 5, prec="fp32", transform="normal")).astype(np.float64)
+    zo = q.points(N, transform=O.NORMAL)
+    assert np.abs(zo).max() > 3.5
+    assert np.max(np.abs(z - zo) / np.maximum(1.0, np.abs(zo))) < 1e-6
+
+
+# ------------------------------------------------------------------ product integrand
+@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX])
+def test_product_theta(R, seq):
+    cfg = inputs.CONFIGS["product_s8"]
+    s, N, M = cfg["s"], cfg["N"], cfg["M"]
+    a = inputs.product_weights(s)
+    th_o = O.product_theta(O.Sequence(seq, s, M, 1, joe_kuo=JK), N, a)
+    th64, rq, sd = R.rqmc_integrate_product(s, N, M, seq, 1, a, prec="fp64")
+    np.testing.assert_allclose(th64, th_o, rtol=1e-13)
+    th32, _, _ = R.rqmc_integrate_product(s, N, M, seq, 1, a, prec="fp32")
+    np.testing.assert_allclose(th32, th_o, rtol=2e-6)
+    assert abs(rq - 1.0) < 4 * sd / np.sqrt(M) + 1e-12
+
+
+# ------------------------------------------------------------------ LMM caplets
+def _caplet_tol(theta_o, nK):
+    """1e-4 max(|theta|, theta_scale) with theta_scale the middle (at-the-money) strike."""
+    t = theta_o.reshape(theta_o.shape[0], -1, nK)
+    scale = np.maximum(np.abs(t), np.abs(t[:, :, nK // 2:nK // 2 + 1]))
+    return 1e-4 * scale.reshape(theta_o.shape)
+
+
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS])
+def test_caplets_small(R, seq):
+    lm = inputs.lmm_flat(40)
+    K = inputs.LMM_STRIKES
+    N, M = 2500, 2
+    th_o = O.lmm_caplets(O.Sequence(seq, 40, M, 3, joe_kuo=JK), lm, K, N)
+    th64, _, _ = R.price_caplets(lm, K, N, M, seq, 3, prec="fp64")
+    np.testing.assert_allclose(th64, th_o, rtol=1e-11, atol=1e-15)
+    th32, _, _ = R.price_caplets(lm, K, N, M, seq, 3, prec="fp32")
+    assert np.all(np.abs(th32 - th_o) <= _caplet_tol(th_o, len(K)))
+
+
+@pytest.mark.parametrize("nf", [1, 7, 16, 23, 80, 160])
+def test_caplets_bucket_edges(R, nf):
+    lm = inputs.lmm_flat(nf, vol=0.2)
+    lm["L0"] = np.linspace(0.04, 0.06, nf + 1)
+    K = np.array([0.05])
+    N, M = 700, 2
+    th_o = O.lmm_caplets(O.Sequence(O.SOBOL_DS, nf, M, 4, joe_kuo=JK), lm, K, N)
+    th64, _, _ = R.price_caplets(lm, K, N, M, O.SOBOL_DS, 4, prec="fp64")
+    np.testing.assert_allclose(th64, th_o, rtol=1e-11, atol=1e-15)
+    th32, _, _ = R.price_caplets(lm, K, N, M, O.SOBOL_DS, 4, prec="fp32")
+    assert np.all(np.abs(th32 - th_o) <= 1e-4 * np.abs(th_o) + 1e-9)
+
+
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX])
+def test_caplets_full_size_sampled(R, seq):
+    """The 40-forward, N = 65536, M = 64 workload as the bench runs it; the oracle
+    recomputes two replications at full N."""
+    cfg = inputs.CONFIGS["lmm_caplets_40"]
+    lm = inputs.lmm_flat(cfg["n_fwd"])
+    K = inputs.LMM_STRIKES
+    N, M = cfg["N"], cfg["M"]
+    th32, rq, sd = R.price_caplets(lm, K, N, M, seq, cfg["seed"], prec="fp32")
+    q = O.Sequence(seq, 40, M, cfg["seed"], joe_kuo=JK)
+    for m in (0, M - 1):
+        th_o = O.lmm_caplets(q, lm, K, N, m_range=(m, m + 1))
+        assert np.all(np.abs(th32[m:m + 1] - th_o) <= _caplet_tol(th_o, len(K)))
+
+
+# ------------------------------------------------------------------ MBS
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS])
+def test_mbs_small(R, seq):
+    mb = inputs.mbs_paper(360)
+    N, M = 1500, 2
+    th_o = O.mbs_theta(O.Sequence(seq, 360, M, 5, joe_kuo=JK), mb, N)
+    th64, _, _ = R.price_mbs(mb, N, M, seq, 5, prec="fp64")
+    np.testing.assert_allclose(th64, th_o, rtol=1e-12)
+    th32, _, _ = R.price_mbs(mb, N, M, seq, 5, prec="fp32")
+    np.testing.assert_allclose(th32, th_o, rtol=1e-4)
+
+
+def test_mbs_full_size_sampled(R):
+    cfg = inputs.CONFIGS["mbs_360"]
+    mb = inputs.mbs_paper(cfg["months"])
+    N, M = cfg["N"], cfg["M"]
+    th32, rq, sd = R.price_mbs(mb, N, M, O.RASRAP, cfg["seed"], prec="fp32")
+    m = M - 1
+    th_o = O.mbs_theta(O.Sequence(O.RASRAP, 360, M, cfg["seed"]), mb, N, m_range=(m, m + 1))
+    np.testing.assert_allclose(th32[m], th_o[0], rtol=1e-4)
+
+
+# ------------------------------------------------------------------ plans and sharding
+def test_offset_shards_add_up(R):
+    import torch
+    lm = inputs.lmm_flat(16)
+    K = inputs.LMM_STRIKES
+    N, M = 4096, 3
+    full = R.Plan.caplets(lm, K, N, M, O.SOBOL_DS, 9, prec="fp64")
+    a = R.Plan.caplets(lm, K, N // 2, M, O.SOBOL_DS, 9, prec="fp64", offset=0)
+    b = R.Plan.caplets(lm, K, N // 2, M, O.SOBOL_DS, 9, prec="fp64", offset=N // 2)
+    tf = full.execute().cpu().numpy()
+    ta, tb = a.execute().cpu().numpy(), b.execute().cpu().numpy()
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(0.5 * (ta + tb), tf, rtol=1e-13, atol=1e-17)
+
+
+def test_plan_is_deterministic_and_launch_knobs_do_not_change_results(R):
+    mb = inputs.mbs_paper(120)
+    p = R.Plan.mbs(mb, 3000, 4, O.RASRAP, 2, prec="fp32")
+    t1 = p.execute().cpu().numpy()
+    t2 = p.execute().cpu().numpy()
+    assert np.array_equal(t1, t2)
+    p.set_launch(threads=128, paths_per_thread=3)
+    t3 = p.execute().cpu().numpy()
+    np.testing.assert_allclose(t3, t1, rtol=1e-5)
+    p.check()
