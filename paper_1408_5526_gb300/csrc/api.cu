@@ -131,23 +131,24 @@ static int lmm_bucket(int nf) {
 template <typename T>
 static void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK, int bucket) {
     const double h = p->delta, sh = std::sqrt(p->delta);
-    const double sc = sizeof(T) == 4 ? 1.4426950408889634 : 1.0;   // FP32 uses exp2
+    const double sc = sizeof(T) == 4 ? 1.4426950408889634 : 1.0;   // FP32 works in base 2
     md = LmmModel<T>{};
     md.nf = p->n_fwd;
     md.nK = nK;
     md.dl = (T)p->delta;
+    md.inv_dl = (T)(1.0 / p->delta);
     md.disc0 = (T)(1.0 / (1.0 + p->delta * p->L0[0]));
+    md.hc = (T)(h * sc);
+    md.sqhc = (T)(sh * sc);
     for (int k = 0; k < nK; ++k) md.K[k] = (T)K[k];
-    const int slot0 = bucket - p->n_fwd;
     for (int slot = 0; slot < bucket; ++slot) {
-        const int n = slot - slot0 + 1;   // forward index
-        const double L0 = n >= 1 ? p->L0[n] : 0.0;
-        const double sg = n >= 1 ? p->vol[n - 1] : 0.0;
-        md.L0[slot] = (T)L0;
-        md.sg[slot] = (T)sg;
-        md.cdr[slot] = (T)(sg * h * sc);
+        const int n = slot + 1;   // forward index; slots beyond nf hold inert padding
+        const bool real = n <= p->n_fwd;
+        const double L0 = real ? p->L0[n] : p->L0[p->n_fwd];
+        const double sg = real ? p->vol[n - 1] : 0.0;
+        md.sig[slot] = (T)sg;
         md.cc[slot] = (T)(-0.5 * sg * sg * h * sc);
-        md.cz[slot] = (T)(sg * sh * sc);
+        md.X0[slot] = (T)(std::log(p->delta * L0) * sc);
     }
 }
 
@@ -165,8 +166,9 @@ static rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, 
         set_error("L0/vol must be finite");
         return RQMC_EINVAL;
     }
-    for (int n = 0; n <= p->n_fwd; ++n)
-        if (!(p->L0[n] > -1.0 / p->delta)) { set_error("1 + delta L0 must be positive"); return RQMC_EINVAL; }
+    if (!(p->L0[0] > -1.0 / p->delta)) { set_error("1 + delta L_0(0) must be positive"); return RQMC_EINVAL; }
+    for (int n = 1; n <= p->n_fwd; ++n)
+        if (!(p->L0[n] > 0.0)) { set_error("log-Euler needs positive initial forwards L_n(0), n >= 1"); return RQMC_EINVAL; }
     if (!K || nK < 1 || nK > kMaxStrikes || !finite_all(K, nK)) {
         set_error("strikes: 1..8 finite values");
         return RQMC_EINVAL;

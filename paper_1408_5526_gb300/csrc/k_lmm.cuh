@@ -1,0 +1,259 @@
+// k_lmm.cuh -- fused LIBOR-market-model caplet kernel (Sec. 5), instantiated per sequence
+// by k_lmm_halton.cu, k_lmm_sobol.cu and k_lmm_philox.cu.
+//
+// One thread = one path of one replication.  Per time step t (grid t_i = T_i, h = delta):
+// coordinate t of the point (Halton/Rasrap digits, Sobol', or Philox) -> Phi^-1 -> one
+// log-Euler step of every alive forward under the spot measure,
+//     log L_n += sigma_n (h mu'_n + sqrt(h) Z) - sigma_n^2 h / 2,
+//     mu'_n = sum_{j=eta}^{n} sigma_j delta L_j / (1 + delta L_j)   (a running prefix),
+// then L_{t+1}(T_{t+1}) is fixed, the spot numeraire is advanced by (1 + delta L_{t+1}) and
+// the caplet payoffs delta (L_{t+1} - K)^+ / prod_{j<=t+1}(1 + delta L_j(T_j)) are staged
+// for the warp reduction.
+//
+// Layout: the forwards live in registers as X_n = log(delta L_n) (base 2 in FP32, so one
+// step of one forward is ex2 + rcp + 5 FP32 ops).  Forward n sits in slot n-1 of an
+// NF-slot array (NF = 16/40/80/160).  Steps run in blocks of 8; after each block the
+// array shifts down by 8 slots, so at step tp of a block the alive slots are tp..7 of
+// group 0 (entered through an 8-way fall-through switch) plus whole groups of 8 that a
+// uniform test skips once they are dead.  The code holds NF update bodies, not NF^2/2.
+// Per-forward constants (sigma_n, -sigma_n^2 h/2) come from shared memory as one 8-byte
+// (FP32) load.  Payoffs are written to a padded per-warp transpose buffer and summed
+// once per block (lane r sums row r), then added to the warp's Kahan accumulator.
+#pragma once
+#include "paths_common.cuh"
+
+namespace rqmc {
+
+template <typename T>
+struct LmmMath;
+// ld.shared of one forward's constants at the point of use (volatile: the compiler
+// must not hoist the 2 x NF constants of a block into registers).
+template <>
+struct LmmMath<float> {
+    using V2 = float2;
+    static constexpr int PAD = 36;   // row stride of the transpose buffer (conflict-free 16-byte reads)
+    static __device__ __forceinline__ float expb(float x) { return ex2_approx(x); }
+    static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
+    static __device__ __forceinline__ float2 lds(const float2 *p) {
+        float2 v;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
+                     : "=f"(v.x), "=f"(v.y)
+                     : "r"((unsigned)__cvta_generic_to_shared(p)));
+        return v;
+    }
+};
+template <>
+struct LmmMath<double> {
+    using V2 = double2;
+    static constexpr int PAD = 34;
+    static __device__ __forceinline__ double expb(double x) { return exp(x); }
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double2 lds(const double2 *p) {
+        double2 v;
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];"
+                     : "=d"(v.x), "=d"(v.y)
+                     : "r"((unsigned)__cvta_generic_to_shared(p)));
+        return v;
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void lmm_update(T &X, const typename LmmMath<T>::V2 c, T &S, T hc, T Az) {
+    const T a = LmmMath<T>::rcp(T(1) + LmmMath<T>::expb(-X));   // delta L / (1 + delta L), old L
+    S = fmaT(c.x, a, S);                                         // prefix including j = n
+    const T w = fmaT(S, hc, Az);
+    X = fmaT(c.x, w, X) + c.y;
+}
+
+template <typename T>
+__device__ __forceinline__ T row_sum32(const T *row) {
+    T s[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int c = 0; c < 32; c += 4) {
+        s[0] += row[c];
+        s[1] += row[c + 1];
+        s[2] += row[c + 2];
+        s[3] += row[c + 3];
+    }
+    return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
+// Shared memory: [generator stage][(sigma, cc) x NF][X0 x NF][normals 8 x threads]
+//                [transpose buffers][acc][cmp]
+template <int NF, typename T>
+__host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, int nw, int nK, int nout,
+                                                           size_t *o_cst, size_t *o_x0, size_t *o_z, size_t *o_buf,
+                                                           size_t *o_acc) {
+    size_t off = stage_bytes(g);
+    *o_cst = off;
+    off = align16(off + sizeof(typename LmmMath<T>::V2) * NF);
+    *o_x0 = off;
+    off = align16(off + sizeof(T) * NF);
+    *o_z = off;
+    off = align16(off + sizeof(T) * 8 * 32 * (size_t)nw);
+    *o_buf = off;
+    off = align16(off + sizeof(T) * (size_t)nw * 8 * nK * LmmMath<T>::PAD);
+    *o_acc = off;
+    off += 2 * sizeof(T) * (size_t)nw * nout;
+    return off;
+}
+
+// CTAs per SM to plan registers for: forwards take NF (FP32) or 2 NF (FP64) registers.
+#ifndef RQMC_LMM_EXTRA_REGS
+#define RQMC_LMM_EXTRA_REGS 44
+#endif
+template <int NF, typename T>
+constexpr int lmm_min_blocks() {
+    constexpr int regs = (int)(NF * sizeof(T) / 4) + RQMC_LMM_EXTRA_REGS;
+    return regs <= 64 ? 4 : regs <= 85 ? 3 : regs <= 128 ? 2 : 1;
+}
+
+template <int NF, int SEQ, typename T>
+__global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kernel(const GenParams g, const LmmModel<T> md, const RedParams r) {
+    using M = LmmMath<T>;
+    using V2 = typename M::V2;
+    constexpr int PAD = M::PAD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nK = md.nK, nout = r.nout, nf = md.nf;
+    size_t o_cst, o_x0, o_z, o_buf, o_acc;
+    lmm_smem_layout<NF, T>(g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
+    T *zb = reinterpret_cast<T *>(smem_raw + o_z) + threadIdx.x;   // [8][blockDim], own column
+    V2 *cst = reinterpret_cast<V2 *>(smem_raw + o_cst);
+    T *X0 = reinterpret_cast<T *>(smem_raw + o_x0);
+    T *wbuf = reinterpret_cast<T *>(smem_raw + o_buf) + (size_t)warp * 8 * nK * PAD;
+    T *acc = reinterpret_cast<T *>(smem_raw + o_acc);
+    T *cmp = acc + nw * nout;
+    T *wacc = acc + warp * nout, *wcmp = cmp + warp * nout;
+    for (int k = threadIdx.x; k < NF; k += blockDim.x) {
+        cst[k] = V2{md.sig[k], md.cc[k]};
+        X0[k] = md.X0[k];
+    }
+    zero_acc(acc, cmp, nw * nout);
+    uint32_t u0, u1;
+    unit_range(r, u0, u1);
+    GenView gv;
+    int staged_m = -1;
+    const T hc = md.hc, sqhc = md.sqhc, inv_dl = md.inv_dl, dl = md.dl;
+    for (uint32_t u = u0; u < u1; ++u) {
+        const int m = (int)(u / r.tiles_per_m);
+        const uint32_t tile = u % r.tiles_per_m;
+        if (m != staged_m) {
+            __syncthreads();
+            stage_tables(g, m, smem_raw, gv);
+            staged_m = m;
+        }
+        __syncthreads();
+        for (int pp = 0; pp < r.ppt; ++pp) {
+            const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
+            const bool active = i < r.N;
+            if (!__any_sync(0xffffffffu, active)) break;
+            PathGen<SEQ> pg;
+            pg.init(gv, active ? i : 0u);
+            T X[NF];
+#pragma unroll
+            for (int k = 0; k < NF; ++k) X[k] = X0[k];
+            T disc = md.disc0;
+            const int nblk = (nf + 7) >> 3;
+            for (int b = 0; b < nblk; ++b) {
+                const int ngrp = (nf - 8 * b + 7) >> 3;   // groups of 8 shifted slots still alive
+                const V2 *cb = cst + 8 * b;               // constants of original slot 8b + k
+                const int nst = min(8, nf - 8 * b);
+                // phase A: the block's normals (one short generator loop)
+                for (int tp = 0; tp < nst; ++tp) zb[tp * blockDim.x] = Draw<T>::normal(pg, 8 * b + tp);
+                // phase B: forward updates and payoffs (each thread reads back its own column)
+                for (int tp = 0; tp < nst; ++tp) {
+                    const T Az = sqhc * zb[tp * blockDim.x];
+                    T S = T(0);
+                    // group 0: alive slots tp..7, entered through a fall-through switch
+                    switch (tp) {
+#define RQMC_G0(k)                                                   \
+    case (k):                                                        \
+        lmm_update<T>(X[(k)], M::lds(cb + (k)), S, hc, Az);
+                        RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
+#undef RQMC_G0
+                        default:
+                            break;
+                    }
+#pragma unroll
+                    for (int gi = 1; gi < NF / 8; ++gi) {
+                        if (gi < ngrp) {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) lmm_update<T>(X[8 * gi + k], M::lds(cb + 8 * gi + k), S, hc, Az);
+                        }
+                    }
+                    // L_{t+1}(T_{t+1}) = b^X / delta sits in shifted slot tp
+                    T Xf = X[0];
+                    switch (tp) {
+#define RQMC_PK(k) \
+    case (k):      \
+        Xf = X[(k)]; \
+        break;
+                        RQMC_PK(1) RQMC_PK(2) RQMC_PK(3) RQMC_PK(4) RQMC_PK(5) RQMC_PK(6) RQMC_PK(7)
+#undef RQMC_PK
+                        default:
+                            break;
+                    }
+                    const T e = M::expb(Xf);
+                    disc *= M::rcp(T(1) + e);
+                    const T Lf = e * inv_dl, dd = dl * disc;
+                    T *row = wbuf + (size_t)tp * nK * PAD + lane;
+                    for (int kk = 0; kk < nK; ++kk) {
+                        const T x = Lf - md.K[kk];
+                        row[kk * PAD] = (active && x > T(0)) ? x * dd : T(0);
+                    }
+                }
+                __syncwarp();
+                const int nrows = nst * nK;
+                for (int rw = lane; rw < nrows; rw += 32) {
+                    const T v = row_sum32<T>(wbuf + (size_t)rw * PAD);
+                    const int o = 8 * b * nK + rw;
+                    T s = wacc[o], c = wcmp[o];
+                    if constexpr (sizeof(T) == 4) kahan_add(s, c, v);
+                    else s += v;
+                    wacc[o] = s;
+                    wcmp[o] = c;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int k = 0; k + 8 < NF; ++k) X[k] = X[k + 8];
+            }
+        }
+        flush_unit(r, u, acc, cmp);
+    }
+}
+
+template <int NF, int SEQ, typename T>
+static cudaError_t launch_lmm_t(const Plan &pl, const LmmModel<T> &md, cudaStream_t st) {
+    auto kern = lmm_caplet_kernel<NF, SEQ, T>;
+    const int threads = pl.threads;
+    size_t a, b, c, d, e2;
+    const size_t smem = lmm_smem_layout<NF, T>(pl.gen, threads / 32, md.nK, pl.red.nout, &a, &b, &c, &d, &e2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (occ < 1) occ = 1;
+    unsigned grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)occ * sms);
+    if (pl.grid > 0) grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)pl.grid);
+    kern<<<grid, threads, smem, st>>>(pl.gen, md, pl.red);
+    return cudaGetLastError();
+}
+
+template <int SEQ>
+cudaError_t launch_caplets_seq(const Plan &pl, cudaStream_t st) {
+    const bool f32 = pl.prec == RQMC_FP32;
+    switch (pl.nf_bucket) {
+        case 16: return f32 ? launch_lmm_t<16, SEQ>(pl, pl.lmm32, st) : launch_lmm_t<16, SEQ>(pl, pl.lmm64, st);
+        case 40: return f32 ? launch_lmm_t<40, SEQ>(pl, pl.lmm32, st) : launch_lmm_t<40, SEQ>(pl, pl.lmm64, st);
+        case 80: return f32 ? launch_lmm_t<80, SEQ>(pl, pl.lmm32, st) : launch_lmm_t<80, SEQ>(pl, pl.lmm64, st);
+        case 160: return f32 ? launch_lmm_t<160, SEQ>(pl, pl.lmm32, st) : launch_lmm_t<160, SEQ>(pl, pl.lmm64, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace rqmc

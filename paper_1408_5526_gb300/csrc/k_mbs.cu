@@ -19,11 +19,11 @@ __device__ __forceinline__ double mbs_exp<double>(double x) { return exp(x); }
 __device__ __forceinline__ float mbs_atan(float x) { return atanf(x); }
 __device__ __forceinline__ double mbs_atan(double x) { return atan(x); }
 
-template <typename T>
-__device__ __forceinline__ T mbs_path(PathGen &pg, const MbsModel<T> &md, const T *__restrict__ ck) {
+template <typename T, int SEQ>
+__device__ __forceinline__ T mbs_path(PathGen<SEQ> &pg, const MbsModel<T> &md, const T *__restrict__ ck) {
     T ip = md.i0, u = md.u1, rr = T(1), v = T(0), vc = T(0);
     for (int k = 1; k <= md.months; ++k) {
-        const T z = NormalOf<T>::get(pg, k - 1);
+        const T z = Draw<T>::normal(pg, k - 1);
         const T ik = ip * mbs_exp<T>(fmaT(md.sz, z, md.lk0));
         const T w = fmaT(md.K2, mbs_atan(fmaT(md.K3, ik, md.K4)), md.K1);
         const T mk = md.c * rr * ((T(1) - w) + w * ck[k]);
@@ -36,39 +36,50 @@ __device__ __forceinline__ T mbs_path(PathGen &pg, const MbsModel<T> &md, const 
     return v - vc;
 }
 
-template <typename T>
+template <typename T, int SEQ>
 __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsModel<T> md, const RedParams r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *acc = reinterpret_cast<T *>(smem_raw);
+    T *acc = reinterpret_cast<T *>(smem_raw + stage_bytes(g));
     T *cmp = acc + nw;
     T *ck = cmp + nw;
     for (int k = threadIdx.x; k <= md.months; k += blockDim.x) ck[k] = md.ck[k];
     zero_acc(acc, cmp, nw);
-    __syncthreads();
     uint32_t u0, u1;
     unit_range(r, u0, u1);
+    GenView gv;
+    int staged_m = -1;
     for (uint32_t u = u0; u < u1; ++u) {
         const int m = (int)(u / r.tiles_per_m);
         const uint32_t tile = u % r.tiles_per_m;
+        if (m != staged_m) {
+            __syncthreads();
+            stage_tables(g, m, smem_raw, gv);
+            staged_m = m;
+        }
+        __syncthreads();
         for (int pp = 0; pp < r.ppt; ++pp) {
             const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
             const bool active = i < r.N;
             if (!__any_sync(0xffffffffu, active)) break;
-            PathGen pg;
-            pg.init(g, m, active ? i : 0u);
-            const T v = mbs_path<T>(pg, md, ck);
+            PathGen<SEQ> pg;
+            pg.init(gv, active ? i : 0u);
+            const T v = mbs_path<T, SEQ>(pg, md, ck);
             warp_accumulate<T>(active ? v : T(0), acc + warp, cmp + warp, 0, lane);
         }
         flush_unit(r, u, acc, cmp);
     }
 }
 
-template <typename T>
+template <typename T, int SEQ>
 static cudaError_t launch_mbs_t(const Plan &pl, const MbsModel<T> &md, cudaStream_t st) {
-    auto kern = mbs_kernel<T>;
+    auto kern = mbs_kernel<T, SEQ>;
     const int threads = pl.threads;
-    const size_t smem = (2ull * (threads / 32) + md.months + 1) * sizeof(T);
+    const size_t smem = stage_bytes(pl.gen) + (2ull * (threads / 32) + md.months + 1) * sizeof(T);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     int occ = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -80,8 +91,15 @@ static cudaError_t launch_mbs_t(const Plan &pl, const MbsModel<T> &md, cudaStrea
     return cudaGetLastError();
 }
 
+template <int SEQ>
+static cudaError_t launch_mbs_seq(const Plan &pl, cudaStream_t st) {
+    return pl.prec == RQMC_FP32 ? launch_mbs_t<float, SEQ>(pl, pl.mbs32, st) : launch_mbs_t<double, SEQ>(pl, pl.mbs64, st);
+}
+
 cudaError_t launch_mbs(const Plan &pl, cudaStream_t st) {
-    return pl.prec == RQMC_FP32 ? launch_mbs_t(pl, pl.mbs32, st) : launch_mbs_t(pl, pl.mbs64, st);
+#define RQMC_L(S) launch_mbs_seq<S>(pl, st)
+    return RQMC_SEQ_DISPATCH(pl.seq, RQMC_L);
+#undef RQMC_L
 }
 
 }  // namespace rqmc

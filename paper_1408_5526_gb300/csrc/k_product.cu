@@ -4,29 +4,36 @@
 
 namespace rqmc {
 
-template <typename T>
+template <typename T, int SEQ>
 __global__ void __launch_bounds__(256) product_kernel(const GenParams g, const ProductModel<T> md,
                                                       const RedParams r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T *acc = reinterpret_cast<T *>(smem_raw);
+    T *acc = reinterpret_cast<T *>(smem_raw + stage_bytes(g));
     T *cmp = acc + nw;
     zero_acc(acc, cmp, nw);
-    __syncthreads();
     uint32_t u0, u1;
     unit_range(r, u0, u1);
+    GenView gv;
+    int staged_m = -1;
     for (uint32_t u = u0; u < u1; ++u) {
         const int m = (int)(u / r.tiles_per_m);
         const uint32_t tile = u % r.tiles_per_m;
+        if (m != staged_m) {
+            __syncthreads();
+            stage_tables(g, m, smem_raw, gv);
+            staged_m = m;
+        }
+        __syncthreads();
         for (int pp = 0; pp < r.ppt; ++pp) {
             const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
             const bool active = i < r.N;
             if (!__any_sync(0xffffffffu, active)) break;
-            PathGen pg;
-            pg.init(g, m, active ? i : 0u);
+            PathGen<SEQ> pg;
+            pg.init(gv, active ? i : 0u);
             T f = T(1);
             for (int j = 0; j < md.s; ++j) {
-                const T x = UniformOf<T>::get(pg, j);
+                const T x = Draw<T>::uniform(pg, j);
                 f *= (fabs(T(4) * x - T(2)) + md.a[j]) * md.inv1pa[j];
             }
             warp_accumulate<T>(active ? f : T(0), acc + warp, cmp + warp, 0, lane);
@@ -35,11 +42,15 @@ __global__ void __launch_bounds__(256) product_kernel(const GenParams g, const P
     }
 }
 
-template <typename T>
+template <typename T, int SEQ>
 static cudaError_t launch_product_t(const Plan &pl, const ProductModel<T> &md, cudaStream_t st) {
-    auto kern = product_kernel<T>;
+    auto kern = product_kernel<T, SEQ>;
     const int threads = pl.threads;
-    const size_t smem = 2ull * (threads / 32) * sizeof(T);
+    const size_t smem = stage_bytes(pl.gen) + 2ull * (threads / 32) * sizeof(T);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
     int occ = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -51,8 +62,16 @@ static cudaError_t launch_product_t(const Plan &pl, const ProductModel<T> &md, c
     return cudaGetLastError();
 }
 
+template <int SEQ>
+static cudaError_t launch_product_seq(const Plan &pl, cudaStream_t st) {
+    return pl.prec == RQMC_FP32 ? launch_product_t<float, SEQ>(pl, pl.prod32, st)
+                                : launch_product_t<double, SEQ>(pl, pl.prod64, st);
+}
+
 cudaError_t launch_product(const Plan &pl, cudaStream_t st) {
-    return pl.prec == RQMC_FP32 ? launch_product_t(pl, pl.prod32, st) : launch_product_t(pl, pl.prod64, st);
+#define RQMC_L(S) launch_product_seq<S>(pl, st)
+    return RQMC_SEQ_DISPATCH(pl.seq, RQMC_L);
+#undef RQMC_L
 }
 
 // theta[m][o] = (sum over the tiles of replication m, in tile order) / N

@@ -64,34 +64,28 @@ __device__ __forceinline__ void warp_accumulate<double>(double v, double *acc, d
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 
-// Uniform u = (num + 1/2)/D of dimension j for the current path.
+// Uniform u = (num + 1/2)/D and normal z of dimension j for the current path.
 template <typename T>
-struct UniformOf;
+struct Draw;
 template <>
-struct UniformOf<float> {
-    static __device__ __forceinline__ float get(PathGen &pg, int j) {
+struct Draw<float> {
+    template <int SEQ>
+    static __device__ __forceinline__ float uniform(PathGen<SEQ> &pg, int j) {
         const Unif32 v = pg.unif32(j);
         return v.lower ? v.q : 1.0f - v.q;
     }
+    template <int SEQ>
+    static __device__ __forceinline__ float normal(PathGen<SEQ> &pg, int j) { return ndtri32(pg.unif32(j)); }
 };
 template <>
-struct UniformOf<double> {
-    static __device__ __forceinline__ double get(PathGen &pg, int j) {
+struct Draw<double> {
+    template <int SEQ>
+    static __device__ __forceinline__ double uniform(PathGen<SEQ> &pg, int j) {
         const Unif64 v = pg.unif64(j);
         return v.lower ? v.q : 1.0 - v.q;
     }
-};
-
-// Normal of dimension j for the current path, in the path precision.
-template <typename T>
-struct NormalOf;
-template <>
-struct NormalOf<float> {
-    static __device__ __forceinline__ float get(PathGen &pg, int j) { return ndtri32(pg.unif32(j)); }
-};
-template <>
-struct NormalOf<double> {
-    static __device__ __forceinline__ double get(PathGen &pg, int j) { return ndtri64(pg.unif64(j)); }
+    template <int SEQ>
+    static __device__ __forceinline__ double normal(PathGen<SEQ> &pg, int j) { return ndtri64(pg.unif64(j)); }
 };
 
 template <typename T>

@@ -109,7 +109,71 @@ struct GenParams {
     const uint32_t *sobV;    // [s][32]
     const uint32_t *sobShift;// [M][s]
     int sob_bits;            // bits of offset + N - 1
+    int stage_sig;           // 1: a replication's permutations are staged in shared memory
 };
+
+// Per-replication view of the generator tables used by the path kernels; the tables
+// of replication m are staged in shared memory when the CTA starts working on m
+// (the permutations only when they fit, see stage_bytes()).
+struct GenView {
+    int seq, s, sob_bits;
+    uint32_t key0, key1, inst;
+    int m;
+    unsigned long long offset;
+    const HaltonDim *hd;     // [s]
+    const uint16_t *sig;     // permutations of replication m
+    const uint32_t *V;       // [s][32]
+    const uint32_t *shift;   // [s]
+};
+
+__host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// Shared-memory bytes the staging of one replication's tables takes.
+__host__ __device__ __forceinline__ size_t stage_bytes(const GenParams &g) {
+    if (g.seq == kHaltonRS || g.seq == kRasrap)
+        return align16(sizeof(HaltonDim) * g.s) + (g.stage_sig ? align16(2 * g.sig_len) : 0);
+    if (g.seq == kSobolDS) return align16(4ull * 32 * g.s) + align16(4ull * g.s);
+    return 0;
+}
+
+// All threads of the CTA call this (no barrier inside; the caller synchronises).
+__device__ __forceinline__ void stage_tables(const GenParams &g, int m, unsigned char *sm, GenView &v) {
+    v.seq = g.seq;
+    v.s = g.s;
+    v.sob_bits = g.sob_bits;
+    v.key0 = g.key0;
+    v.key1 = g.key1;
+    v.inst = g.inst;
+    v.m = m;
+    v.offset = g.offset;
+    v.hd = nullptr;
+    v.sig = nullptr;
+    v.V = nullptr;
+    v.shift = nullptr;
+    if (g.seq == kHaltonRS || g.seq == kRasrap) {
+        HaltonDim *hd = reinterpret_cast<HaltonDim *>(sm);
+        const uint4 *src = reinterpret_cast<const uint4 *>(g.hdim + (size_t)m * g.s);
+        uint4 *dst = reinterpret_cast<uint4 *>(hd);
+        const int n16 = (int)(sizeof(HaltonDim) / 16) * g.s;
+        for (int k = threadIdx.x; k < n16; k += blockDim.x) dst[k] = src[k];
+        v.hd = hd;
+        const uint16_t *gs = g.sigma + (size_t)m * g.sig_len;
+        if (g.stage_sig) {
+            uint16_t *ss = reinterpret_cast<uint16_t *>(sm + align16(sizeof(HaltonDim) * g.s));
+            for (unsigned long long k = threadIdx.x; k < g.sig_len; k += blockDim.x) ss[k] = gs[k];
+            v.sig = ss;
+        } else {
+            v.sig = gs;
+        }
+    } else if (g.seq == kSobolDS) {
+        uint32_t *V = reinterpret_cast<uint32_t *>(sm);
+        uint32_t *sh = reinterpret_cast<uint32_t *>(sm + align16(4ull * 32 * g.s));
+        for (int k = threadIdx.x; k < 32 * g.s; k += blockDim.x) V[k] = g.sobV[k];
+        for (int k = threadIdx.x; k < g.s; k += blockDim.x) sh[k] = g.sobShift[(size_t)m * g.s + k];
+        v.V = V;
+        v.shift = sh;
+    }
+}
 
 // ------------------------------------------------------------------ Halton digits
 // Digits of low = lo0 + i in base p, each mapped through sigma and accumulated in
@@ -119,8 +183,12 @@ __device__ __forceinline__ uint32_t halton_R(const HaltonDim &h, const uint16_t 
     uint32_t low = h.lo0 + i;
     carry = low >= h.pL ? 1u : 0u;
     low -= carry ? h.pL : 0u;
-    uint32_t r = 0;
     const uint16_t *sg = sig + h.sig_off;
+    if (h.p == 2) {   // base 2: the digits are bits and sigma is the identity or the swap
+        const uint32_t rev = __brev(low) >> (32u - h.L);
+        return sg[0] != 0 ? rev ^ ((1u << h.L) - 1u) : rev;
+    }
+    uint32_t r = 0;
     for (uint32_t k = 0; k < h.L; ++k) {
         uint32_t q = __umulhi(low, h.magic);
         uint32_t d = low - q * h.p;
@@ -128,7 +196,7 @@ __device__ __forceinline__ uint32_t halton_R(const HaltonDim &h, const uint16_t 
             d += h.p;
             q -= 1;
         }
-        r = r * h.p + (uint32_t)__ldg(sg + d);
+        r = r * h.p + (uint32_t)sg[d];
         low = q;
     }
     return r;
@@ -151,7 +219,7 @@ __device__ __forceinline__ uint32_t sobol_x(const uint32_t *__restrict__ V, uint
     uint32_t x = shift;
 #pragma unroll 4
     for (int k = 0; k < nbits; ++k)
-        if ((n >> k) & 1u) x ^= __ldg(V + k);
+        if ((n >> k) & 1u) x ^= V[k];
     return x;
 }
 
@@ -190,55 +258,62 @@ __device__ __forceinline__ Unif64 unif64_halton(const HaltonDim &h, uint32_t R, 
     return Unif64{((double)qn + 0.5) * h.invD, lower};
 }
 
-// Stateful per-thread coordinate source for one path (fixed m and point i).
-// Philox words come four dimensions at a time and are cached.
+// Stateful per-thread coordinate source for one path (fixed m and point i) of sequence
+// SEQ (compile time).  Philox words come four dimensions at a time and are cached.
+template <int SEQ>
 struct PathGen {
-    const GenParams *g;
-    int m;
+    GenView v;              // by value: the fields stay in (uniform) registers
     uint32_t i;
     unsigned long long n;   // offset + i
     int blk;
     U32x4 words;
 
-    __device__ __forceinline__ void init(const GenParams &gp, int m_, uint32_t i_) {
-        g = &gp;
-        m = m_;
+    __device__ __forceinline__ void init(const GenView &gv, uint32_t i_) {
+        v = gv;
         i = i_;
-        n = gp.offset + i_;
+        n = gv.offset + i_;
         blk = -1;
     }
     __device__ __forceinline__ uint32_t philox_word(int j) {
         if ((j >> 2) != blk) {
             blk = j >> 2;
             words = philox4x32_10((uint32_t)n, (uint32_t)((n >> 32) & 0xFFFFu) | ((uint32_t)blk << 16),
-                                  (uint32_t)m, kTagPath | (g->inst << 8), g->key0, g->key1);
+                                  (uint32_t)v.m, kTagPath | (v.inst << 8), v.key0, v.key1);
         }
         const int w = j & 3;
         return w == 0 ? words.x : w == 1 ? words.y : w == 2 ? words.z : words.w;
     }
     __device__ __forceinline__ Unif32 unif32(int j) {
-        const int seq = g->seq;
-        if (seq == kPhilox) return unif32_from_u32(philox_word(j));
-        if (seq == kSobolDS)
-            return unif32_from_u32(sobol_x(g->sobV + 32 * j, __ldg(g->sobShift + (size_t)m * g->s + j), (uint32_t)n,
-                                           g->sob_bits));
-        const HaltonDim &h = g->hdim[(size_t)m * g->s + j];
-        uint32_t c;
-        const uint32_t R = halton_R(h, g->sigma + (size_t)m * g->sig_len, i, c);
-        return unif32_halton(h, R, c);
+        if constexpr (SEQ == kPhilox) {
+            return unif32_from_u32(philox_word(j));
+        } else if constexpr (SEQ == kSobolDS) {
+            return unif32_from_u32(sobol_x(v.V + 32 * j, v.shift[j], (uint32_t)n, v.sob_bits));
+        } else {
+            const HaltonDim &h = v.hd[j];
+            uint32_t c;
+            const uint32_t R = halton_R(h, v.sig, i, c);
+            return unif32_halton(h, R, c);
+        }
     }
     __device__ __forceinline__ Unif64 unif64(int j) {
-        const int seq = g->seq;
-        if (seq == kPhilox) return unif64_from_u32(philox_word(j));
-        if (seq == kSobolDS)
-            return unif64_from_u32(sobol_x(g->sobV + 32 * j, __ldg(g->sobShift + (size_t)m * g->s + j), (uint32_t)n,
-                                           g->sob_bits));
-        const HaltonDim &h = g->hdim[(size_t)m * g->s + j];
-        uint32_t c;
-        const uint32_t R = halton_R(h, g->sigma + (size_t)m * g->sig_len, i, c);
-        return unif64_halton(h, R, c);
+        if constexpr (SEQ == kPhilox) {
+            return unif64_from_u32(philox_word(j));
+        } else if constexpr (SEQ == kSobolDS) {
+            return unif64_from_u32(sobol_x(v.V + 32 * j, v.shift[j], (uint32_t)n, v.sob_bits));
+        } else {
+            const HaltonDim &h = v.hd[j];
+            uint32_t c;
+            const uint32_t R = halton_R(h, v.sig, i, c);
+            return unif64_halton(h, R, c);
+        }
     }
 };
+
+// Runtime sequence -> compile-time generator (HALTON_RS and RASRAP share one code path).
+#define RQMC_SEQ_DISPATCH(seq, F)              \
+    ((seq) == kPhilox    ? F(kPhilox)          \
+     : (seq) == kSobolDS ? F(kSobolDS)         \
+                         : F(kRasrap))
 
 // ------------------------------------------------------------------ inverse normal CDF
 // erfinv(y)/y as a polynomial in w = -ln(4q(1-q)) (three branches, coefficients

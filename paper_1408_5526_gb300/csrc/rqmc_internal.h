@@ -29,17 +29,18 @@ struct RedParams {
     uint32_t *status;        // device status word (0 = ok)
 };
 
+// One-factor LMM in log space: X_n = log(delta L_n) (FP32: log2), so that
+// delta L/(1 + delta L) = 1/(1 + b^-X) and one log-Euler step is
+// X_n += sigma_n (h S_n + sqrt(h) Z) - sigma_n^2 h / 2 (times log2 e in FP32).
 template <typename T>
 struct LmmModel {
     int nf, nK;
-    T dl;                    // delta
-    T disc0;                 // 1 / (1 + delta L_0(0))
+    T dl, inv_dl, disc0;     // delta, 1/delta, 1/(1 + delta L_0(0))
+    T hc, sqhc;              // h, sqrt(h)               (FP32: times log2 e)
     T K[kMaxStrikes];
-    T L0[kMaxFwd];           // L_1(0) .. L_nf(0)
-    T sg[kMaxFwd];           // sigma_n (one factor)
-    T cdr[kMaxFwd];          // drift coefficient sigma_n h        (FP32: times log2 e)
-    T cc[kMaxFwd];           // -sigma_n^2 h / 2                    (FP32: times log2 e)
-    T cz[kMaxFwd];           // sigma_n sqrt(h)                     (FP32: times log2 e)
+    T sig[kMaxFwd];          // sigma_n at slot n-1 (zero beyond nf)
+    T cc[kMaxFwd];           // -sigma_n^2 h / 2         (FP32: times log2 e)
+    T X0[kMaxFwd];           // log(delta L_n(0))        (FP32: log2)
 };
 
 template <typename T>

@@ -253,6 +253,7 @@ rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint
         g.hdim = reinterpret_cast<const HaltonDim *>(d + gl.hdim_off);
         g.sigma = reinterpret_cast<const uint16_t *>(d + gl.sigma_off);
         g.sig_len = gl.sig_len;
+        g.stage_sig = 2ull * gl.sig_len <= 48ull * 1024 ? 1 : 0;
         BaseConst *db = reinterpret_cast<BaseConst *>(d + gl.base_off);
         if (cudaMemcpyAsync(db, gl.bases.data(), sizeof(BaseConst) * s, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return RQMC_ECUDA;
