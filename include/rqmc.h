@@ -168,6 +168,23 @@ rqmc_status price_adjoint(const rqmc_lmm_params *p, const double *strikes_host, 
 rqmc_status price_batch(const rqmc_instrument *inst, int n, int M, rqmc_sequence seq, uint64_t seed,
                         rqmc_precision prec, double *theta_host, void *stream);
 
+/* ---------------------------------------------------------------- pricing without allocation */
+
+/* The caplet values of price_caplets written to theta_dev [M][nf*n_strikes] (device
+ * memory), asynchronously on `stream`, WITHOUT allocating anything.  The paper has no
+ * counterpart: this entry point serves callers that cannot allocate device memory at the
+ * moment they price (inside a CUDA graph capture, inside another framework's allocator
+ * callback, or under a no-allocation-after-start-up policy).  Its scratch space is one
+ * 16 MiB array built into the library, created on every GPU that loads the library and
+ * held until the process exits; a request whose tables and partial sums need more returns
+ * RQMC_EINVAL with the size in rqmc_last_error().  The first call on each device looks up
+ * that array's device address and caches it: make it before any stream capture starts.
+ * All calls share the array, so calls whose work overlaps on the GPU race and must be
+ * serialised by the caller.  Same argument limits as price_caplets (one factor). */
+rqmc_status rqmc_price_caplets_noalloc(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes,
+                                       int64_t N, int M, rqmc_sequence seq, uint64_t seed, rqmc_precision prec,
+                                       double *theta_dev, void *stream);
+
 /* ---------------------------------------------------------------- plans (device resident) */
 
 /* Build randomization tables and model constants on the device once; every

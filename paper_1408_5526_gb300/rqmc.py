@@ -33,7 +33,7 @@ EXPORTS = ["rqmc_set_sobol_table", "rqmc_points", "rqmc_integrate_product", "pri
            "price_adjoint", "price_batch", "rqmc_plan_product", "rqmc_plan_caplets", "rqmc_plan_mbs",
            "rqmc_plan_adjoint", "rqmc_plan_batch", "rqmc_plan_output_size", "rqmc_plan_launches",
            "rqmc_plan_set_launch", "rqmc_plan_execute", "rqmc_plan_check", "rqmc_plan_destroy",
-           "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version"]
+           "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version", "rqmc_price_caplets_noalloc"]
 
 
 class RqmcError(RuntimeError):
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH):
         L.price_mbs.argtypes = [C.POINTER(MbsParams), i64, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, dp, dp, vp]
         L.price_adjoint.argtypes = [C.POINTER(LmmParams), dp, C.c_int, dp, i64, C.c_int, C.c_int, C.c_uint64,
                                     C.c_int, C.c_int, dp, dp, dp, vp]
+        L.rqmc_price_caplets_noalloc.argtypes = [C.POINTER(LmmParams), dp, C.c_int, i64, C.c_int, C.c_int,
+                                                 C.c_uint64, C.c_int, dp, vp]
         L.price_batch.argtypes = [C.POINTER(Instrument), C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, dp, vp]
         pp = C.POINTER(vp)
         L.rqmc_plan_product.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int, C.c_uint64, dp, C.c_int, pp]
@@ -198,6 +200,20 @@ def price_mbs(mbs: dict, N, M, seq, seed, prec="fp32", stream=None):
     _check(L, L.price_mbs(C.byref(p), N, M, _enum(seq, _SEQ), seed, _enum(prec, _PREC), _dp(th), _dp(rq), _dp(sd),
                           _stream(stream)))
     return th[:, 0], rq[0], sd[0]
+
+
+def price_caplets_noalloc(lmm: dict, strikes, N, M, seq, seed, theta, prec="fp32", stream=None):
+    """Caplet values into the device tensor `theta` [M, n_fwd*n_strikes] (float64) with no
+    allocation by the library (scratch is a fixed 16 MiB array inside it); asynchronous."""
+    L = load()
+    keep: list = []
+    p = _lmm_struct(lmm, keep)
+    K = np.ascontiguousarray(strikes, dtype=np.float64)
+    _check(L, L.rqmc_price_caplets_noalloc(C.byref(p), _dp(K), len(K), N, M, _enum(seq, _SEQ), seed,
+                                           _enum(prec, _PREC),
+                                           C.cast(C.c_void_p(theta.data_ptr()), C.POINTER(C.c_double)),
+                                           _stream(stream)))
+    return theta
 
 
 # ------------------------------------------------------------------ plans
