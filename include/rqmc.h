@@ -153,9 +153,11 @@ rqmc_status price_mbs(const rqmc_mbs_params *p, int64_t N, int M, rqmc_sequence 
                       rqmc_precision prec, double *theta_host, double *rq_host, double *sd_host, void *stream);
 
 /* Pathwise adjoint of the caplet strip V = sum_{n,k} w_{n,k} caplet_{n,k} (not in the
- * paper): value_host[M], delta_host[M][nf] = dV/dL_n(0), vega_host[M][nf] = dV/dvol_n with
- * b_n fixed, per replication.  weights_host[nf*n_strikes].  Checkpoints the forward
- * path every `checkpoint` steps (0 = library choice, about sqrt(nf)). */
+ * paper; the model and estimator are Sec. 5's): value_host[M], delta_host[M][nf] =
+ * dV/dL_n(0), vega_host[M][nf] = dV/dvol_n with the loadings b_n fixed, per replication.
+ * weights_host[nf*n_strikes].  FP32 paths, nf <= 80, d in {1, 2}.  The forward sweep
+ * records every step's drift factors in per-thread device scratch (`checkpoint` must be
+ * 0 or 1); the reverse sweep regenerates the normals from the counter. */
 rqmc_status price_adjoint(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes,
                           const double *weights_host, int64_t N, int M, rqmc_sequence seq, uint64_t seed,
                           rqmc_precision prec, int checkpoint, double *value_host, double *delta_host,
@@ -203,7 +205,9 @@ rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double *strikes_ho
                               uint64_t seed, rqmc_precision prec, int checkpoint, rqmc_plan **plan);
 rqmc_status rqmc_plan_batch(const rqmc_instrument *inst, int n, int M, rqmc_sequence seq, uint64_t seed,
                             rqmc_precision prec, rqmc_plan **plan);
-/* Number of doubles the plan writes per execute (M*n_out; adjoint: M*(1+2*nf)). */
+/* Number of doubles the plan writes per execute, M*n_out.  Adjoint plans write per
+ * replication [value, dV/dL_n(0) (nf), dV/dvol_n (nf), unweighted caplet values (nf*n_strikes)];
+ * with all weights zero they skip the reverse sweep and act as a d-factor caplet pricer. */
 int64_t rqmc_plan_output_size(const rqmc_plan *plan);
 /* Kernel launches one execute performs (for launch accounting). */
 int rqmc_plan_launches(const rqmc_plan *plan);

@@ -118,6 +118,11 @@ static size_t partial_capacity(const Plan &pl, int nout) {
 static void destroy(Plan *pl, cudaStream_t st) {
     if (!pl) return;
     if (pl->d_buf) cudaFreeAsync(pl->d_buf, st);
+    if (pl->adj_buf) {
+        cudaStreamSynchronize(st);
+        cudaFree(pl->adj_buf);
+    }
+    delete pl->adjm;
     delete pl;
 }
 
@@ -331,6 +336,10 @@ extern "C" int rqmc_plan_launches(const rqmc_plan *plan) { return plan ? plan->l
 
 extern "C" rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int paths_per_thread) {
     if (!plan) { set_error("plan is NULL"); return RQMC_EINVAL; }
+    if (plan->kind == kAdjoint) {
+        set_error("adjoint plans size their per-thread scratch for a fixed launch shape");
+        return RQMC_EUNSUPPORTED;
+    }
     int t = threads > 0 ? threads : plan->threads;
     int p = paths_per_thread > 0 ? paths_per_thread : plan->ppt;
     if (t % 32 != 0 || t < 32 || t > 256 || p < 1 || p > 64) {
@@ -353,6 +362,7 @@ extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, voi
         case kProduct: e = launch_product(*plan, st); break;
         case kCaplets: e = launch_caplets(*plan, st); break;
         case kMbs: e = launch_mbs(*plan, st); break;
+        case kAdjoint: e = launch_adjoint(*plan, st); break;
         default: set_error("plan kind cannot be executed"); return RQMC_EUNSUPPORTED;
     }
     if (e != cudaSuccess) return cuda_fail(e, "path kernel launch");
@@ -463,18 +473,120 @@ extern "C" rqmc_status price_mbs(const rqmc_mbs_params *p, int64_t N, int M, rqm
     return run_oneshot(pl, theta_host, rq_host, sd_host, stream);
 }
 
-// ------------------------------------------------------------------ not yet built in this file
-extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *, const double *, int, const double *, int64_t,
-                                         int64_t, int, rqmc_sequence, uint64_t, rqmc_precision, int, rqmc_plan **) {
-    set_error("adjoint plans are not built yet");
-    return RQMC_EUNSUPPORTED;
+// ------------------------------------------------------------------ pathwise adjoint
+extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes,
+                                         const double *weights_host, int64_t N, int64_t offset, int M,
+                                         rqmc_sequence seq, uint64_t seed, rqmc_precision prec, int checkpoint,
+                                         rqmc_plan **plan) {
+    rqmc_status rs = check_lmm(p, strikes_host, n_strikes, true);
+    if (rs != RQMC_OK) return rs;
+    if (p->n_fwd > kMaxAdjFwd) { set_error("adjoint: n_fwd must be <= 80"); return RQMC_EUNSUPPORTED; }
+    if (prec != RQMC_FP32) { set_error("adjoint: FP32 paths only"); return RQMC_EUNSUPPORTED; }
+    if (checkpoint < 0 || checkpoint > 1) {
+        set_error("adjoint: checkpoint must be 0 or 1 (the forward sweep records every step)");
+        return RQMC_EINVAL;
+    }
+    const int nf = p->n_fwd, d = p->n_factors;
+    if (!weights_host || !finite_all(weights_host, nf * n_strikes)) {
+        set_error("adjoint: n_fwd * n_strikes finite weights required");
+        return RQMC_EINVAL;
+    }
+    if (d == 2 && !finite_all(p->loadings, 2 * nf)) { set_error("adjoint: loadings must be finite"); return RQMC_EINVAL; }
+    rqmc_plan *pl = nullptr;
+    rs = new_plan(kAdjoint, nf * d, N, offset, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    const int nout = 1 + 2 * nf + nf * n_strikes;
+    pl->nf_bucket = nf <= 40 ? 40 : 80;
+    pl->checkpoint = 1;
+    set_reduction(*pl, nout, 128, 4);
+    AdjModel *md = new AdjModel();
+    std::memset(md, 0, sizeof(AdjModel));
+    pl->adjm = md;
+    const double l2e = 1.4426950408889634, h = p->delta;
+    md->nf = nf;
+    md->nK = n_strikes;
+    md->d = d;
+    md->dl = (float)p->delta;
+    md->inv_dl = (float)(1.0 / p->delta);
+    md->disc0 = (float)(1.0 / (1.0 + p->delta * p->L0[0]));
+    md->h = (float)h;
+    md->sqh = (float)std::sqrt(h);
+    bool any_w = false;
+    for (int k = 0; k < n_strikes; ++k) md->K[k] = (float)strikes_host[k];
+    for (int n = 0; n < pl->nf_bucket; ++n) {
+        const bool real = n < nf;
+        double b0 = 1.0, b1 = 0.0;
+        if (real && d == 2) { b0 = p->loadings[2 * n]; b1 = p->loadings[2 * n + 1]; }
+        const double vol = real ? p->vol[n] : 0.0;
+        const double L0 = real ? p->L0[n + 1] : p->L0[nf];
+        md->sg[n][0] = (float)(vol * b0);
+        md->sg[n][1] = (float)(vol * b1);
+        md->b[n][0] = (float)b0;
+        md->b[n][1] = (float)b1;
+        md->cc[n] = (float)(-0.5 * h * vol * vol * (b0 * b0 + b1 * b1) * l2e);
+        md->X0[n] = (float)(std::log2(p->delta * L0));
+        md->invL0ln2[n] = (float)(1.0 / (L0 * 0.6931471805599453));
+        if (real)
+            for (int k = 0; k < n_strikes; ++k) {
+                md->w[n][k] = (float)weights_host[n * n_strikes + k];
+                any_w = any_w || weights_host[n * n_strikes + k] != 0.0;
+            }
+    }
+    md->reverse = any_w ? 1 : 0;
+    rs = finish_plan(pl, {}, 16, (size_t)pl->red.units * nout, 0, nullptr);
+    if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
+    pl->grid = adjoint_grid(*pl);
+    if (pl->grid < 1) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
+    // per-thread records: per step 1 + (8 ngrp - tp) floats
+    size_t E = 0;
+    for (int b = 0; b < (nf + 7) / 8; ++b) {
+        const int ngrp = (nf - 8 * b + 7) / 8;
+        for (int tp = 0; tp < std::min(8, nf - 8 * b); ++tp) E += 1 + 8 * ngrp - tp;
+    }
+    const uint32_t T = (uint32_t)pl->grid * (uint32_t)pl->threads;
+    const size_t rows = 1 + 2 * (size_t)pl->nf_bucket + (size_t)nf * n_strikes;
+    pl->adjs.T = T;
+    const size_t bytes = sizeof(float) * ((size_t)E + rows) * T;
+    void *buf = nullptr;
+    cudaError_t e = cudaMalloc(&buf, bytes);
+    if (e != cudaSuccess) { destroy(pl, 0); set_error("adjoint: scratch allocation failed"); return RQMC_ENOMEM; }
+    pl->adj_buf = buf;
+    pl->adjs.store = static_cast<float *>(buf);
+    pl->adjs.acc = static_cast<float *>(buf) + (size_t)E * T;
+    if ((e = cudaMemset(pl->adjs.acc, 0, sizeof(float) * rows * T)) != cudaSuccess) {
+        destroy(pl, 0);
+        return cuda_fail(e, "adjoint scratch clear");
+    }
+    pl->launches = 2;
+    *plan = pl;
+    return RQMC_OK;
 }
-extern "C" rqmc_status price_adjoint(const rqmc_lmm_params *, const double *, int, const double *, int64_t, int,
-                                     rqmc_sequence, uint64_t, rqmc_precision, int, double *, double *, double *,
-                                     void *) {
-    set_error("price_adjoint is not built yet");
-    return RQMC_EUNSUPPORTED;
+
+extern "C" rqmc_status price_adjoint(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes,
+                                     const double *weights_host, int64_t N, int M, rqmc_sequence seq, uint64_t seed,
+                                     rqmc_precision prec, int checkpoint, double *value_host, double *delta_host,
+                                     double *vega_host, void *stream) {
+    if (!value_host || !delta_host || !vega_host) { set_error("adjoint outputs are required"); return RQMC_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_oneshot_mu);
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs =
+        rqmc_plan_adjoint(p, strikes_host, n_strikes, weights_host, N, 0, M, seq, seed, prec, checkpoint, &pl);
+    if (rs != RQMC_OK) return rs;
+    const int nf = p->n_fwd, nout = pl->nout;
+    std::vector<double> th((size_t)M * nout);
+    rs = run_oneshot(pl, th.data(), nullptr, nullptr, stream);
+    if (rs != RQMC_OK) return rs;
+    for (int m = 0; m < M; ++m) {
+        const double *row = th.data() + (size_t)m * nout;
+        value_host[m] = row[0];
+        for (int n = 0; n < nf; ++n) {
+            delta_host[(size_t)m * nf + n] = row[1 + n];
+            vega_host[(size_t)m * nf + n] = row[1 + nf + n];
+        }
+    }
+    return RQMC_OK;
 }
+
 extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *, int, int, rqmc_sequence, uint64_t, rqmc_precision,
                                        rqmc_plan **) {
     set_error("batch plans are not built yet");

@@ -70,6 +70,30 @@ struct BaseConst {
     double invD;
 };
 
+constexpr int kMaxAdjFwd = 80;   // forwards of an adjoint strip (register buckets 40/80)
+
+// Two-factor-capable LMM for the pathwise adjoint (FP32 paths).
+struct AdjModel {
+    int nf, nK, d;
+    int reverse;                         // 0: prices only (all weights zero)
+    float dl, inv_dl, disc0;
+    float h, sqh;                        // h = delta, sqrt(h)
+    float K[kMaxStrikes];
+    float w[kMaxAdjFwd][kMaxStrikes];    // caplet weights w_{n,k} (row n-1)
+    float sg[kMaxAdjFwd][2];             // sigma_n = vol_n b_n (zero beyond nf)
+    float b[kMaxAdjFwd][2];              // unit loadings b_n
+    float cc[kMaxAdjFwd];                // -h |sigma_n|^2 / 2 times log2 e
+    float X0[kMaxAdjFwd];                // log2(delta L_n(0))
+    float invL0ln2[kMaxAdjFwd];          // 1 / (L_n(0) ln 2)
+};
+
+// Per-thread global columns of the adjoint kernel (column stride T = threads in the grid).
+struct AdjScratch {
+    float *store;   // forward-sweep records: per step the fixed forward's pre-step X, then the a_n
+    float *acc;     // [1 + 2 NF + nf nK] rows: value, dV/dL_n(0), dV/dvol_n, caplet prices
+    uint32_t T;
+};
+
 enum PlanKind { kPoints = 0, kProduct = 1, kCaplets = 2, kMbs = 3, kAdjoint = 4, kBatch = 5 };
 
 struct BatchPlan;
@@ -99,7 +123,9 @@ struct Plan {
     ProductModel<double> prod64{};
     // adjoint
     int checkpoint = 0;
-    void *adj = nullptr;
+    AdjModel *adjm = nullptr;
+    AdjScratch adjs{};
+    void *adj_buf = nullptr;          // per-thread scratch columns (cudaMalloc)
     BatchPlan *batch = nullptr;
     int device = 0;
 };
@@ -133,6 +159,8 @@ cudaError_t launch_product(const Plan &pl, cudaStream_t st);
 cudaError_t launch_caplets(const Plan &pl, cudaStream_t st);
 cudaError_t launch_mbs(const Plan &pl, cudaStream_t st);
 cudaError_t launch_theta(const Plan &pl, double *theta_dev, cudaStream_t st);
+cudaError_t launch_adjoint(const Plan &pl, cudaStream_t st);
+int adjoint_grid(const Plan &pl);
 int occupancy_blocks(const Plan &pl);
 
 // ---- errors

@@ -202,6 +202,20 @@ def price_mbs(mbs: dict, N, M, seq, seed, prec="fp32", stream=None):
     return th[:, 0], rq[0], sd[0]
 
 
+def price_adjoint(lmm: dict, strikes, weights, N, M, seq, seed, prec="fp32", stream=None):
+    """Per replication: value of V = sum w_{n,k} caplet_{n,k}, dV/dL_n(0) and dV/dvol_n."""
+    L = load()
+    keep: list = []
+    p = _lmm_struct(lmm, keep)
+    K = np.ascontiguousarray(strikes, dtype=np.float64)
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+    nf = p.n_fwd
+    value, delta, vega = np.zeros(M), np.zeros((M, nf)), np.zeros((M, nf))
+    _check(L, L.price_adjoint(C.byref(p), _dp(K), len(K), _dp(w), N, M, _enum(seq, _SEQ), seed, _enum(prec, _PREC), 0,
+                              _dp(value), _dp(delta), _dp(vega), _stream(stream)))
+    return value, delta, vega
+
+
 def price_caplets_noalloc(lmm: dict, strikes, N, M, seq, seed, theta, prec="fp32", stream=None):
     """Caplet values into the device tensor `theta` [M, n_fwd*n_strikes] (float64) with no
     allocation by the library (scratch is a fixed 16 MiB array inside it); asynchronous."""
@@ -254,6 +268,19 @@ class Plan:
                                   C.byref(h)))
         return cls(h, M, 1)
 
+    @classmethod
+    def adjoint(cls, lmm, strikes, weights, N, M, seq, seed, prec="fp32", offset=0):
+        """Outputs per replication: [value, dV/dL_n(0) (nf), dV/dvol_n (nf), caplet prices (nf*nK)]."""
+        L = load()
+        keep: list = []
+        p = _lmm_struct(lmm, keep)
+        K = np.ascontiguousarray(strikes, dtype=np.float64)
+        w = np.ascontiguousarray(weights, dtype=np.float64).reshape(-1)
+        h = C.c_void_p()
+        _check(L, L.rqmc_plan_adjoint(C.byref(p), _dp(K), len(K), _dp(w), N, offset, M, _enum(seq, _SEQ), seed,
+                                      _enum(prec, _PREC), 0, C.byref(h)))
+        return cls(h, M, 1 + 2 * p.n_fwd + p.n_fwd * len(K))
+
     def output_size(self):
         return int(load().rqmc_plan_output_size(self._h))
 
@@ -285,3 +312,46 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ autograd
+def _caplet_strip_function():
+    import torch
+
+    class CapletStrip(torch.autograd.Function):
+        """Caplet prices RQ_{M,N} [n_fwd * n_strikes] as a function of the initial forwards
+        L_n(0) (n = 1..nf) and the vols; the backward pass is the library's pathwise adjoint
+        with grad_output as the caplet weights."""
+
+        @staticmethod
+        def forward(ctx, L0, vol, lmm, strikes, N, M, seq, seed):
+            lm = dict(lmm)
+            full = np.array(lmm["L0"], dtype=np.float64).copy()
+            full[1:] = L0.detach().cpu().numpy()
+            lm["L0"] = full
+            lm["vol"] = vol.detach().cpu().numpy().astype(np.float64)
+            K = np.asarray(strikes, dtype=np.float64)
+            nf = int(lm["n_fwd"])
+            zero = np.zeros(nf * len(K))
+            plan = Plan.adjoint(lm, K, zero, N, M, seq, seed)
+            out = plan.execute().cpu().numpy().reshape(M, -1)
+            plan.close()
+            prices = out[:, 1 + 2 * nf:].mean(axis=0)
+            ctx.args = (lm, K, N, M, seq, seed)
+            return torch.as_tensor(prices, dtype=L0.dtype, device=L0.device)
+
+        @staticmethod
+        def backward(ctx, grad):
+            lm, K, N, M, seq, seed = ctx.args
+            w = grad.detach().cpu().numpy().astype(np.float64)
+            _, delta, vega = price_adjoint(lm, K, w, N, M, seq, seed)
+            dL = torch.as_tensor(delta.mean(axis=0), dtype=grad.dtype, device=grad.device)
+            dv = torch.as_tensor(vega.mean(axis=0), dtype=grad.dtype, device=grad.device)
+            return dL, dv, None, None, None, None, None, None
+
+    return CapletStrip
+
+
+def caplet_strip(L0, vol, lmm: dict, strikes, N, M, seq, seed):
+    """Differentiable caplet prices: see CapletStrip."""
+    return _caplet_strip_function().apply(L0, vol, lmm, strikes, N, M, seq, seed)
