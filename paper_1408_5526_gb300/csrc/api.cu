@@ -117,6 +117,7 @@ static size_t partial_capacity(const Plan &pl, int nout) {
 
 static void destroy(Plan *pl, cudaStream_t st) {
     if (!pl) return;
+    if (pl->kind == kBatch) batch_destroy(*pl);
     if (pl->d_buf) cudaFreeAsync(pl->d_buf, st);
     if (pl->adj_buf) {
         cudaStreamSynchronize(st);
@@ -329,6 +330,7 @@ extern "C" rqmc_status rqmc_plan_mbs(const rqmc_mbs_params *p, int64_t N, int64_
 
 extern "C" int64_t rqmc_plan_output_size(const rqmc_plan *plan) {
     if (!plan) return -1;
+    if (plan->kind == kBatch) return batch_output_size(*plan);
     return (int64_t)plan->M * plan->nout;
 }
 
@@ -336,8 +338,8 @@ extern "C" int rqmc_plan_launches(const rqmc_plan *plan) { return plan ? plan->l
 
 extern "C" rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int paths_per_thread) {
     if (!plan) { set_error("plan is NULL"); return RQMC_EINVAL; }
-    if (plan->kind == kAdjoint) {
-        set_error("adjoint plans size their per-thread scratch for a fixed launch shape");
+    if (plan->kind == kAdjoint || plan->kind == kBatch) {
+        set_error("adjoint and batch plans fix their launch shape when they are built");
         return RQMC_EUNSUPPORTED;
     }
     int t = threads > 0 ? threads : plan->threads;
@@ -357,6 +359,7 @@ extern "C" rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int pa
 extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, void *stream) {
     if (!plan || !theta_dev) { set_error("plan and theta_dev are required"); return RQMC_EINVAL; }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->kind == kBatch) return batch_execute(*plan, theta_dev, st);
     cudaError_t e;
     switch (plan->kind) {
         case kProduct: e = launch_product(*plan, st); break;
@@ -373,6 +376,10 @@ extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, voi
 extern "C" rqmc_status rqmc_plan_check(rqmc_plan *plan, void *stream) {
     if (!plan) { set_error("plan is NULL"); return RQMC_EINVAL; }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (plan->kind == kBatch) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        return e == cudaSuccess ? RQMC_OK : cuda_fail(e, "batch");
+    }
     uint32_t h[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(h, reinterpret_cast<unsigned char *>(plan->red.status) - sizeof(uint32_t),
                                     sizeof(h), cudaMemcpyDeviceToHost, st);
@@ -587,13 +594,25 @@ extern "C" rqmc_status price_adjoint(const rqmc_lmm_params *p, const double *str
     return RQMC_OK;
 }
 
-extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *, int, int, rqmc_sequence, uint64_t, rqmc_precision,
-                                       rqmc_plan **) {
-    set_error("batch plans are not built yet");
-    return RQMC_EUNSUPPORTED;
-}
-extern "C" rqmc_status price_batch(const rqmc_instrument *, int, int, rqmc_sequence, uint64_t, rqmc_precision,
-                                   double *, void *) {
-    set_error("price_batch is not built yet");
-    return RQMC_EUNSUPPORTED;
+extern "C" rqmc_status price_batch(const rqmc_instrument *inst, int n, int M, rqmc_sequence seq, uint64_t seed,
+                                   rqmc_precision prec, double *theta_host, void *stream) {
+    if (!theta_host) { set_error("theta_host is NULL"); return RQMC_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_oneshot_mu);
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs = rqmc_plan_batch(inst, n, M, seq, seed, prec, &pl);
+    if (rs != RQMC_OK) return rs;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t nd = rqmc_plan_output_size(pl);
+    double *theta_dev = nullptr;
+    cudaError_t e = cudaMallocAsync(&theta_dev, sizeof(double) * nd, st);
+    if (e != cudaSuccess) { destroy(pl, st); set_error("device allocation failed"); return RQMC_ENOMEM; }
+    rs = rqmc_plan_execute(pl, theta_dev, stream);
+    if (rs == RQMC_OK) {
+        e = cudaMemcpyAsync(theta_host, theta_dev, sizeof(double) * nd, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rs = cuda_fail(e, "batch result copy");
+    }
+    cudaFreeAsync(theta_dev, st);
+    destroy(pl, st);
+    return rs;
 }

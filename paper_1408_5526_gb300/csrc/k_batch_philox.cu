@@ -1,0 +1,6 @@
+// k_batch_philox.cu -- batched persistent kernel for the philox generator.
+#include "k_batch.cuh"
+
+namespace rqmc {
+template cudaError_t launch_batch_seq<kPhilox>(const BatchLaunch &bl, cudaStream_t st);
+}  // namespace rqmc

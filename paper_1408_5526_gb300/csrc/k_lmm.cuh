@@ -78,7 +78,14 @@ __device__ __forceinline__ T row_sum32(const T *row) {
     return (s[0] + s[1]) + (s[2] + s[3]);
 }
 
-// Shared memory: [generator stage][(sigma, cc) x NF][X0 x NF][normals 8 x threads]
+// Scalars of one LMM caplet strip as the path code uses them.
+template <typename T>
+struct LmmScal {
+    int nf, nK;
+    T dl, inv_dl, disc0, hc, sqhc;
+};
+
+// Shared memory: [generator stage][(sigma, cc) x NF][X0 x NF, K x 8][normals 8 x threads]
 //                [transpose buffers][acc][cmp]
 template <int NF, typename T>
 __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, int nw, int nK, int nout,
@@ -88,7 +95,7 @@ __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, i
     *o_cst = off;
     off = align16(off + sizeof(typename LmmMath<T>::V2) * NF);
     *o_x0 = off;
-    off = align16(off + sizeof(T) * NF);
+    off = align16(off + sizeof(T) * (NF + kMaxStrikes));
     *o_z = off;
     off = align16(off + sizeof(T) * 8 * 32 * (size_t)nw);
     *o_buf = off;
@@ -108,6 +115,87 @@ constexpr int lmm_min_blocks() {
     return regs <= 64 ? 4 : regs <= 85 ? 3 : regs <= 128 ? 2 : 1;
 }
 
+// One path: forwards in registers, per-step payoffs into the warp's transpose buffer,
+// block sums into the warp's Kahan accumulators (wacc/wcmp, indexed by output t nK + k).
+template <int NF, int SEQ, typename T>
+__device__ __forceinline__ void lmm_path(PathGen<SEQ> &pg, const bool active, const LmmScal<T> &sc,
+                                         const typename LmmMath<T>::V2 *cst, const T *X0, const T *Ks, T *zb,
+                                         T *wbuf, T *wacc, T *wcmp, const int lane) {
+    using M = LmmMath<T>;
+    using V2 = typename M::V2;
+    constexpr int PAD = M::PAD;
+    const int nf = sc.nf, nK = sc.nK;
+    const T hc = sc.hc, sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
+    T X[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) X[k] = X0[k];
+    T disc = sc.disc0;
+    const int nblk = (nf + 7) >> 3;
+    for (int b = 0; b < nblk; ++b) {
+        const int ngrp = (nf - 8 * b + 7) >> 3;   // groups of 8 shifted slots still alive
+        const V2 *cb = cst + 8 * b;               // constants of original slot 8b + k
+        const int nst = min(8, nf - 8 * b);
+        // phase A: the block's normals (one short generator loop)
+        for (int tp = 0; tp < nst; ++tp) zb[tp * blockDim.x] = Draw<T>::normal(pg, 8 * b + tp);
+        // phase B: forward updates and payoffs (each thread reads back its own column)
+        for (int tp = 0; tp < nst; ++tp) {
+            const T Az = sqhc * zb[tp * blockDim.x];
+            T S = T(0);
+            // group 0: alive slots tp..7, entered through a fall-through switch
+            switch (tp) {
+#define RQMC_G0(k)                                                   \
+    case (k):                                                        \
+        lmm_update<T>(X[(k)], M::lds(cb + (k)), S, hc, Az);
+                RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
+#undef RQMC_G0
+                default:
+                    break;
+            }
+#pragma unroll
+            for (int gi = 1; gi < NF / 8; ++gi) {
+                if (gi < ngrp) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) lmm_update<T>(X[8 * gi + k], M::lds(cb + 8 * gi + k), S, hc, Az);
+                }
+            }
+            // L_{t+1}(T_{t+1}) = b^X / delta sits in shifted slot tp
+            T Xf = X[0];
+            switch (tp) {
+#define RQMC_PK(k) \
+    case (k):      \
+        Xf = X[(k)]; \
+        break;
+                RQMC_PK(1) RQMC_PK(2) RQMC_PK(3) RQMC_PK(4) RQMC_PK(5) RQMC_PK(6) RQMC_PK(7)
+#undef RQMC_PK
+                default:
+                    break;
+            }
+            const T e = M::expb(Xf);
+            disc *= M::rcp(T(1) + e);
+            const T Lf = e * inv_dl, dd = dl * disc;
+            T *row = wbuf + (size_t)tp * nK * PAD + lane;
+            for (int kk = 0; kk < nK; ++kk) {
+                const T x = Lf - Ks[kk];
+                row[kk * PAD] = (active && x > T(0)) ? x * dd : T(0);
+            }
+        }
+        __syncwarp();
+        const int nrows = nst * nK;
+        for (int rw = lane; rw < nrows; rw += 32) {
+            const T v = row_sum32<T>(wbuf + (size_t)rw * PAD);
+            const int o = 8 * b * nK + rw;
+            T s = wacc[o], c = wcmp[o];
+            if constexpr (sizeof(T) == 4) kahan_add(s, c, v);
+            else s += v;
+            wacc[o] = s;
+            wcmp[o] = c;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k + 8 < NF; ++k) X[k] = X[k + 8];
+    }
+}
+
 template <int NF, int SEQ, typename T>
 __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kernel(const GenParams g, const LmmModel<T> md, const RedParams r) {
     using M = LmmMath<T>;
@@ -115,12 +203,13 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     constexpr int PAD = M::PAD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nK = md.nK, nout = r.nout, nf = md.nf;
+    const int nK = md.nK, nout = r.nout;
     size_t o_cst, o_x0, o_z, o_buf, o_acc;
     lmm_smem_layout<NF, T>(g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
     T *zb = reinterpret_cast<T *>(smem_raw + o_z) + threadIdx.x;   // [8][blockDim], own column
     V2 *cst = reinterpret_cast<V2 *>(smem_raw + o_cst);
     T *X0 = reinterpret_cast<T *>(smem_raw + o_x0);
+    T *Ks = X0 + NF;
     T *wbuf = reinterpret_cast<T *>(smem_raw + o_buf) + (size_t)warp * 8 * nK * PAD;
     T *acc = reinterpret_cast<T *>(smem_raw + o_acc);
     T *cmp = acc + nw * nout;
@@ -129,12 +218,13 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
         cst[k] = V2{md.sig[k], md.cc[k]};
         X0[k] = md.X0[k];
     }
+    if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md.K[threadIdx.x];
     zero_acc(acc, cmp, nw * nout);
+    const LmmScal<T> sc{md.nf, md.nK, md.dl, md.inv_dl, md.disc0, md.hc, md.sqhc};
     uint32_t u0, u1;
     unit_range(r, u0, u1);
     GenView gv;
     int staged_m = -1;
-    const T hc = md.hc, sqhc = md.sqhc, inv_dl = md.inv_dl, dl = md.dl;
     for (uint32_t u = u0; u < u1; ++u) {
         const int m = (int)(u / r.tiles_per_m);
         const uint32_t tile = u % r.tiles_per_m;
@@ -150,74 +240,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
             if (!__any_sync(0xffffffffu, active)) break;
             PathGen<SEQ> pg;
             pg.init(gv, active ? i : 0u);
-            T X[NF];
-#pragma unroll
-            for (int k = 0; k < NF; ++k) X[k] = X0[k];
-            T disc = md.disc0;
-            const int nblk = (nf + 7) >> 3;
-            for (int b = 0; b < nblk; ++b) {
-                const int ngrp = (nf - 8 * b + 7) >> 3;   // groups of 8 shifted slots still alive
-                const V2 *cb = cst + 8 * b;               // constants of original slot 8b + k
-                const int nst = min(8, nf - 8 * b);
-                // phase A: the block's normals (one short generator loop)
-                for (int tp = 0; tp < nst; ++tp) zb[tp * blockDim.x] = Draw<T>::normal(pg, 8 * b + tp);
-                // phase B: forward updates and payoffs (each thread reads back its own column)
-                for (int tp = 0; tp < nst; ++tp) {
-                    const T Az = sqhc * zb[tp * blockDim.x];
-                    T S = T(0);
-                    // group 0: alive slots tp..7, entered through a fall-through switch
-                    switch (tp) {
-#define RQMC_G0(k)                                                   \
-    case (k):                                                        \
-        lmm_update<T>(X[(k)], M::lds(cb + (k)), S, hc, Az);
-                        RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
-#undef RQMC_G0
-                        default:
-                            break;
-                    }
-#pragma unroll
-                    for (int gi = 1; gi < NF / 8; ++gi) {
-                        if (gi < ngrp) {
-#pragma unroll
-                            for (int k = 0; k < 8; ++k) lmm_update<T>(X[8 * gi + k], M::lds(cb + 8 * gi + k), S, hc, Az);
-                        }
-                    }
-                    // L_{t+1}(T_{t+1}) = b^X / delta sits in shifted slot tp
-                    T Xf = X[0];
-                    switch (tp) {
-#define RQMC_PK(k) \
-    case (k):      \
-        Xf = X[(k)]; \
-        break;
-                        RQMC_PK(1) RQMC_PK(2) RQMC_PK(3) RQMC_PK(4) RQMC_PK(5) RQMC_PK(6) RQMC_PK(7)
-#undef RQMC_PK
-                        default:
-                            break;
-                    }
-                    const T e = M::expb(Xf);
-                    disc *= M::rcp(T(1) + e);
-                    const T Lf = e * inv_dl, dd = dl * disc;
-                    T *row = wbuf + (size_t)tp * nK * PAD + lane;
-                    for (int kk = 0; kk < nK; ++kk) {
-                        const T x = Lf - md.K[kk];
-                        row[kk * PAD] = (active && x > T(0)) ? x * dd : T(0);
-                    }
-                }
-                __syncwarp();
-                const int nrows = nst * nK;
-                for (int rw = lane; rw < nrows; rw += 32) {
-                    const T v = row_sum32<T>(wbuf + (size_t)rw * PAD);
-                    const int o = 8 * b * nK + rw;
-                    T s = wacc[o], c = wcmp[o];
-                    if constexpr (sizeof(T) == 4) kahan_add(s, c, v);
-                    else s += v;
-                    wacc[o] = s;
-                    wcmp[o] = c;
-                }
-                __syncwarp();
-#pragma unroll
-                for (int k = 0; k + 8 < NF; ++k) X[k] = X[k + 8];
-            }
+            lmm_path<NF, SEQ, T>(pg, active, sc, cst, X0, Ks, zb, wbuf, wacc, wcmp, lane);
         }
         flush_unit(r, u, acc, cmp);
     }

@@ -94,6 +94,33 @@ struct AdjScratch {
     uint32_t T;
 };
 
+// One instrument of a batched launch (device copy).
+struct BatchInst {
+    GenParams g;                      // its randomization tables (instrument index in the counters)
+    int kind;                         // 0 LMM caplet strip, 1 MBS
+    int bucket;                       // LMM register bucket
+    int nout;                         // outputs per replication
+    uint32_t N, tiles_per_m;
+    unsigned long long part_off;      // first partial row, in doubles
+    unsigned long long theta_off;     // first theta value, in doubles
+    const LmmModel<float> *lmm;
+    const MbsModel<float> *mbs;
+};
+
+struct BatchItem {
+    uint32_t inst, m, tile, pad;
+};
+
+struct BatchLaunch {
+    const BatchInst *insts;
+    const BatchItem *items;
+    uint32_t n_items, n_inst;
+    uint32_t *counter;
+    double *partials, *theta;
+    int threads, ppt;
+    size_t smem;
+};
+
 enum PlanKind { kPoints = 0, kProduct = 1, kCaplets = 2, kMbs = 3, kAdjoint = 4, kBatch = 5 };
 
 struct BatchPlan;
@@ -160,6 +187,11 @@ cudaError_t launch_caplets(const Plan &pl, cudaStream_t st);
 cudaError_t launch_mbs(const Plan &pl, cudaStream_t st);
 cudaError_t launch_theta(const Plan &pl, double *theta_dev, cudaStream_t st);
 cudaError_t launch_adjoint(const Plan &pl, cudaStream_t st);
+cudaError_t launch_batch(const BatchLaunch &bl, int seq, cudaStream_t st);
+rqmc_status batch_execute(Plan &pl, double *theta_dev, cudaStream_t st);
+int64_t batch_output_size(const Plan &pl);
+void batch_destroy(Plan &pl);
+int batch_ppt(const Plan &pl);
 int adjoint_grid(const Plan &pl);
 int occupancy_blocks(const Plan &pl);
 

@@ -216,6 +216,43 @@ def price_adjoint(lmm: dict, strikes, weights, N, M, seq, seed, prec="fp32", str
     return value, delta, vega
 
 
+def _instruments(insts) -> "C.Array":
+    """Batch descriptors from dicts: {"kind": "lmm", "n_fwd", "N", "rate", "vol", "strike"} or
+    {"kind": "mbs", "months", "N", mbs constants (defaults: the paper's)}."""
+    arr = (Instrument * len(insts))()
+    for a, d in zip(arr, insts):
+        if d["kind"] == "lmm":
+            a.kind, a.size = 0, int(d["n_fwd"])
+            a.rate, a.vol = float(d.get("rate", 0.05)), float(d.get("vol", 0.15))
+            a.strike = float(d.get("strike", a.rate))
+        else:
+            a.kind, a.size = 1, int(d["months"])
+            mb = dict(inputs.mbs_paper(int(d["months"])), **{k: v for k, v in d.items() if k in
+                                                              ("i0", "K1", "K2", "K3", "K4", "sigma", "c")})
+            a.mbs = _mbs_struct(mb)
+        a.N = int(d["N"])
+    return arr
+
+
+def _split_batch(theta, insts, M):
+    out, off = [], 0
+    for d in insts:
+        nout = int(d["n_fwd"]) if d["kind"] == "lmm" else 1
+        out.append(np.asarray(theta[off:off + M * nout]).reshape(M, nout))
+        off += M * nout
+    return out
+
+
+def price_batch(insts, M, seq, seed, prec="fp32", stream=None):
+    """Per instrument a theta array [M, n_out] (n_out = n_fwd caplets or 1 MBS value)."""
+    L = load()
+    arr = _instruments(insts)
+    n_total = sum(M * (int(d["n_fwd"]) if d["kind"] == "lmm" else 1) for d in insts)
+    th = np.zeros(n_total)
+    _check(L, L.price_batch(arr, len(insts), M, _enum(seq, _SEQ), seed, _enum(prec, _PREC), _dp(th), _stream(stream)))
+    return _split_batch(th, insts, M)
+
+
 def price_caplets_noalloc(lmm: dict, strikes, N, M, seq, seed, theta, prec="fp32", stream=None):
     """Caplet values into the device tensor `theta` [M, n_fwd*n_strikes] (float64) with no
     allocation by the library (scratch is a fixed 16 MiB array inside it); asynchronous."""
@@ -280,6 +317,21 @@ class Plan:
         _check(L, L.rqmc_plan_adjoint(C.byref(p), _dp(K), len(K), _dp(w), N, offset, M, _enum(seq, _SEQ), seed,
                                       _enum(prec, _PREC), 0, C.byref(h)))
         return cls(h, M, 1 + 2 * p.n_fwd + p.n_fwd * len(K))
+
+    @classmethod
+    def batch(cls, insts, M, seq, seed, prec="fp32"):
+        """One persistent graph-captured launch over all instruments; execute() returns the
+        concatenated [M, n_out_i] blocks (use split_batch to separate them)."""
+        L = load()
+        arr = _instruments(insts)
+        h = C.c_void_p()
+        _check(L, L.rqmc_plan_batch(arr, len(insts), M, _enum(seq, _SEQ), seed, _enum(prec, _PREC), C.byref(h)))
+        pl = cls(h, M, 0)
+        pl.insts = list(insts)
+        return pl
+
+    def split_batch(self, theta):
+        return _split_batch(theta.cpu().numpy() if hasattr(theta, "cpu") else theta, self.insts, self.M)
 
     def output_size(self):
         return int(load().rqmc_plan_output_size(self._h))
