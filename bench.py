@@ -45,13 +45,15 @@ def _peaks():
 
 def lmm_algorithmic_ops(nf, nK, paths):
     """Source-level operations of one fused caplet launch.
-    MUFU: rcp + ex2 per forward update, lg2 (inverse CDF) + rcp (numeraire) per step.
-    FP32 pipe: 7 per forward update, 16 per inverse CDF, 2 per numeraire step,
-    4 per strike payoff."""
+    MUFU: ex2 + rcp per forward update; per step lg2 (inverse CDF) and ex2 + rcp
+    (fixed forward and numeraire).  Returned as SFU issue slots: on GB300 ex2 issues at
+    32 per SM per clock and rcp/lg2 at 16, so an ex2 counts half a slot.
+    FP32 pipe: 5 per forward update, 16 per inverse CDF, 4 per step, 4 per strike."""
     upd = nf * (nf + 1) // 2
-    mufu = 2 * upd + 2 * nf
-    fma = 7 * upd + nf * (16 + 2 + 4 * nK)
-    return mufu * paths, fma * paths
+    n_ex2, n_rcp, n_lg2 = upd + nf, upd + nf, nf
+    slots = 0.5 * n_ex2 + n_rcp + n_lg2
+    fma = 5 * upd + nf * (16 + 4 + 4 * nK)
+    return slots * paths, fma * paths
 
 
 class ClockSampler:
@@ -186,19 +188,22 @@ def run_ours(args, rank, world):
 
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    mufu_peak = 16 * 152 * sm_max * 1e6           # MUFU ops/s: 16 per SM per clock
+    mufu_peak = 16 * 152 * sm_max * 1e6           # SFU issue slots/s: 16 per SM per clock
     fma_peak = 128 * 152 * sm_max * 1e6           # FP32 lane-ops/s: 128 per SM per clock
     mufu, fma = lmm_algorithmic_ops(N_FWD, len(K), N_PATHS * M_REPL)
     per_launch_s = statistics.mean(launch_ms) / 1e3
     a_mufu, a_fma = mufu / per_launch_s, fma / per_launch_s
     roof = {"bound": "alu", "pipe": "sfu" if a_mufu / mufu_peak >= a_fma / fma_peak else "fma",
-            "achieved": round(a_mufu / 1e12, 4), "peak": round(mufu_peak / 1e12, 4), "unit": "Tops/s (MUFU)",
+            "achieved": round(a_mufu / 1e12, 4), "peak": round(mufu_peak / 1e12, 4),
+            "unit": "T SFU issue slots/s (ex2 = 1/2 slot, rcp/lg2 = 1 slot)",
             "frac": round(a_mufu / mufu_peak, 4), "traffic": None,
             "fma_achieved": round(a_fma / 1e12, 3), "fma_peak": round(fma_peak / 1e12, 3),
             "fma_frac": round(a_fma / fma_peak, 4),
             "kernel": "lmm_caplet_kernel<40,float> + theta_kernel",
             "launch_ms": round(per_launch_s * 1e3, 4),
-            "peak_source": "derived: 16 MUFU / 128 FP32 lanes per SM per clock x 152 SMs x sm_max_mhz"}
+            "peak_source": "derived: 16 SFU slots / 128 FP32 lanes per SM per clock x 152 SMs x sm_max_mhz "
+                           "(probe: ex2 29.8, rcp 15.1, lg2 15.4 per SM per clock)"}
+    extra = other_workloads(args, dev, seed) if (rank == 0 and not args.no_extra) else None
     cpu = cpu_baseline(args) if (rank == 0 and not args.no_cpu) else None
     clocks = clk.summary()
     if rank == 0:
@@ -222,10 +227,95 @@ def run_ours(args, rank, world):
                     "api": "price_caplets (host buffers) x 3 sequences"},
             "gpu_launches": args.steps * sum(p.launches() for p in plans),
             "clocks": clocks,
+            "workloads": extra,
         }
         print(json.dumps(line), flush=True)
     for p in plans:
         p.close()
+
+
+def _time_plan(execute, reps, flush):
+    import torch
+    for _ in range(3):
+        execute()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        execute()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def other_workloads(args, dev, seed):
+    """The other configurations of the scope, one timed figure each (median of a few
+    launches, L2 flushed before each, inputs resident): product integrand (FP64),
+    LMM caplets in FP64, MBS (FP32), two-factor adjoint Greeks (FP32), the
+    512-instrument batch (FP32, graph launch) and the point stream (HBM write GB/s)."""
+    import torch
+    from paper_1408_5526_gb300 import inputs, rqmc
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    # product integrand, s = 8, N = 4096, M = 32, random-start Halton, FP64
+    p = rqmc.Plan.product(8, 4096, 32, "halton_rs", seed, inputs.product_weights(8), prec="fp64")
+    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+    ms = _time_plan(lambda: p.execute(o), 10, flush)
+    th = o.cpu().numpy()
+    out["product_s8_N4096_M32_fp64"] = {"ms": ms, "path_steps_per_s": 8 * 4096 * 32 / (ms / 1e3),
+                                        "rq": float(th.mean()), "exact": 1.0}
+    p.close()
+    # LMM caplets in FP64 (same 40-forward workload), Rasrap
+    lm = inputs.lmm_flat(N_FWD)
+    p = rqmc.Plan.caplets(lm, inputs.LMM_STRIKES, N_PATHS, M_REPL, "rasrap", seed, prec="fp64")
+    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+    ms = _time_plan(lambda: p.execute(o), 2, flush)
+    out["lmm_caplets_40_N65536_M64_fp64_rasrap"] = {"ms": ms,
+                                                    "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3)}
+    p.close()
+    # MBS, 360 months, N = 65536, M = 64, FP32 + Kahan
+    mb = inputs.mbs_paper(360)
+    res = {}
+    for s_ in SEQS:
+        p = rqmc.Plan.mbs(mb, N_PATHS, M_REPL, s_, seed, prec="fp32")
+        o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+        ms = _time_plan(lambda: p.execute(o), 3, flush)
+        res[s_] = {"ms": ms, "path_steps_per_s": N_PATHS * M_REPL * 360 / (ms / 1e3), "rq": float(o.mean())}
+        p.close()
+    out["mbs_360_N65536_M64_fp32"] = res
+    # adjoint Greeks: two-factor 80-forward strip, N = 2^18, M = 32, FP32 paths
+    l2 = inputs.lmm_two_factor(80, seed=seed)
+    p = rqmc.Plan.adjoint(l2, [0.05], np.ones(80), 1 << 18, 32, "sobol_ds", seed)
+    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+    ms = _time_plan(lambda: p.execute(o), 2, flush)
+    out["adjoint_2f_80_N262144_M32_fp32_sobol"] = {"ms": ms,
+                                                   "path_steps_per_s": (1 << 18) * 32 * 160 / (ms / 1e3)}
+    p.close()
+    # 512-instrument batch, one graph launch
+    desc = inputs.batch_instruments(seed)
+    insts = [dict(d, rate=0.05, vol=0.15, strike=0.05) if d["kind"] == "lmm" else d for d in desc]
+    p = rqmc.Plan.batch(insts, 32, "sobol_ds", seed)
+    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+    ms = _time_plan(lambda: p.execute(o), 1, flush)
+    steps = sum(d["N"] * 32 * (d["n_fwd"] if d["kind"] == "lmm" else d["months"]) for d in desc)
+    out["batch_512_M32_fp32_sobol"] = {"ms": ms, "path_steps_per_s": steps / (ms / 1e3), "path_steps": steps}
+    p.close()
+    # point stream: s = 360, N = 65536, M = 64 FP32 normals, written to HBM
+    buf = torch.empty((M_REPL, 360, N_PATHS), dtype=torch.float32, device=dev)
+    res = {}
+    peaks = _peaks()
+    for s_ in SEQS:
+        ms = _time_plan(lambda: rqmc.rqmc_points(360, N_PATHS, M_REPL, s_, seed, transform="normal", out=buf), 3,
+                        flush)
+        gbs = buf.numel() * 4 / (ms / 1e3) / 1e9
+        res[s_] = {"ms": ms, "GB_per_s": gbs, "frac_of_measured_hbm": gbs / float(peaks.get("hbm_gbs", 6800.0)),
+                   "gnumbers_per_s": buf.numel() / (ms / 1e3) / 1e9}
+    out["points_s360_N65536_M64_fp32_normal"] = res
+    del buf
+    return out
 
 
 def cpu_baseline(args, seconds_hint=True):
@@ -284,6 +374,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--skip-parity", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other-configuration figures")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
