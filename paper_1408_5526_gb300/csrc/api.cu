@@ -544,14 +544,11 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
     if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
     pl->grid = adjoint_grid(*pl);
     if (pl->grid < 1) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
-    // per-thread records: per step 1 + (8 ngrp - tp) floats
+    // per-thread records (float4 units): per step t a header and chunks t/4 .. ceil(nf/4)-1
     size_t E = 0;
-    for (int b = 0; b < (nf + 7) / 8; ++b) {
-        const int ngrp = (nf - 8 * b + 7) / 8;
-        for (int tp = 0; tp < std::min(8, nf - 8 * b); ++tp) E += 1 + 8 * ngrp - tp;
-    }
+    for (int t = 0; t < nf; ++t) E += 4 * (size_t)(1 + (nf + 3) / 4 - t / 4);
     const uint32_t T = (uint32_t)pl->grid * (uint32_t)pl->threads;
-    const size_t rows = 1 + 2 * (size_t)pl->nf_bucket + (size_t)nf * n_strikes;
+    const size_t rows = 1 + 2 * (size_t)pl->nf_bucket + (size_t)nf * n_strikes;   // vega chunks, value, delta, prices
     pl->adjs.T = T;
     const size_t bytes = sizeof(float) * ((size_t)E + rows) * T;
     void *buf = nullptr;

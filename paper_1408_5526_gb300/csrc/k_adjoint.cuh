@@ -7,9 +7,13 @@
 //     a_n = 1 / (1 + 2^-X_n)               (= delta L_n / (1 + delta L_n))
 //     A_n = sum_{j<=n, alive} sigma_j a_j   (d-vector prefix)
 //     X_n += log2 e (h sigma_n.A_n + sqrt(h) sigma_n.Z - h |sigma_n|^2 / 2).
-// Forward sweep (as in the caplet kernel, 8-step blocks with a register shift) stores,
-// per step, the pre-step X of the forward fixed at that step and every updated a_n in a
-// per-thread column of global scratch (coalesced across the warp).  Reverse sweep: with
+// Each thread keeps its path's X_n (then the adjoints) in a shared-memory column and loops
+// over the alive forwards with rolled loops, so the code stays small and about 60
+// registers give ~20 warps per SM.  The forward sweep stores, per step, a header (the
+// pre-step X of the forward fixed at that step, the step's prefix total A) and the a_n in
+// 16-byte chunks aligned to absolute forward slots, interleaved by thread in global scratch:
+// one coalesced 128-bit store (and, in the reverse sweep, one 128-bit load) per four
+// forwards.  The vega accumulators use the same chunking.  Reverse sweep: with
 // Xb_n = dV/dX_n in registers and B_n = sum_{m>=n} Xb_m sigma_m,
 //     sigma_bar_n = log2 e [Xb_n (h A_n + sqrt(h) Z - h sigma_n) + h a_n B_n]
 //     Xb_n       += h (sigma_n.B_n) a_n (1 - a_n)
@@ -24,64 +28,41 @@
 
 namespace rqmc {
 
-template <int D>
-__device__ __forceinline__ float dotv(const float (&x)[D], const float (&y)[D]) {
-    float s = x[0] * y[0];
-    if constexpr (D == 2) s = fmaf(x[1], y[1], s);
-    return s;
-}
-
-__device__ __forceinline__ float4 lds4(const float4 *p) {
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"((unsigned)__cvta_generic_to_shared(p)));
-    return v;
-}
-
 // Shared memory: [generator stage][(sigma_1, sigma_2, b_1, b_2) x NF][cc x NF]
+//                [per-thread state x NF x blockDim]  (forward X, then the adjoints Xb)
 template <int NF>
-__host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, size_t *o_cst, size_t *o_cc) {
+__host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, int threads, size_t *o_cst,
+                                                           size_t *o_cc, size_t *o_st) {
     size_t off = align16(stage_bytes(g));
     *o_cst = off;
     off = align16(off + sizeof(float4) * NF);
     *o_cc = off;
     off = align16(off + sizeof(float) * NF);
+    *o_st = off;
+    off = align16(off + sizeof(float) * NF * (size_t)threads);
     return off;
 }
 
-// one forward step of slot k (forward sweep): store a_k, advance the prefix and X_k
-template <int D>
-__device__ __forceinline__ void adj_fwd_update(float &X, const float4 c, float cc, float (&A)[D], const float (&Az)[D],
-                                               float hl, float *&st, uint32_t T) {
-    const float a = rcp_approx(1.0f + ex2_approx(-X));
-    *st = a;
-    st += T;
-    A[0] = fmaf(c.x, a, A[0]);
-    float inc = fmaf(c.x, fmaf(A[0], hl, Az[0]), cc);
-    if constexpr (D == 2) {
-        A[1] = fmaf(c.y, a, A[1]);
-        inc = fmaf(c.y, fmaf(A[1], hl, Az[1]), inc);
-    }
-    X += inc;
-}
-
 template <int NF, int D, int SEQ>
-__global__ void __launch_bounds__(128, NF <= 40 ? 4 : 2) lmm_adjoint_kernel(const GenParams g, const AdjModel md,
-                                                                            const AdjScratch sc, const RedParams r) {
+__global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, const AdjModel md, const AdjScratch sc,
+                                                         const RedParams r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t o_cst, o_cc;
-    adj_smem_layout<NF>(g, &o_cst, &o_cc);
+    size_t o_cst, o_cc, o_st;
+    adj_smem_layout<NF>(g, blockDim.x, &o_cst, &o_cc, &o_st);
     float4 *cst = reinterpret_cast<float4 *>(smem_raw + o_cst);
     float *ccs = reinterpret_cast<float *>(smem_raw + o_cc);
+    float *xs = reinterpret_cast<float *>(smem_raw + o_st) + threadIdx.x;   // slot n at xs[n * blockDim]
+    const int bd = blockDim.x;
     for (int k = threadIdx.x; k < NF; k += blockDim.x) {
         cst[k] = make_float4(md.sg[k][0], md.sg[k][1], md.b[k][0], md.b[k][1]);
         ccs[k] = md.cc[k];
     }
     const uint32_t T = sc.T;                              // threads in the grid: column stride
     const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
-    float *acc = sc.acc + gt;                             // [1 + 2 NF] rows: value, delta, vega
-    const int nf = md.nf, nK = md.nK;
+    // accumulators: vega as float4 chunks [NF/4][T], then value [T], delta [NF][T], prices [nf nK][T]
+    float4 *__restrict__ vega4 = reinterpret_cast<float4 *>(sc.acc) + gt;
+    float *accs = sc.acc + (size_t)NF * T + gt;
+    const int nf = md.nf, nK = md.nK, nch = (nf + 3) >> 2;
     const float l2e = 1.4426950408889634f, ln2 = 0.6931471805599453f;
     const float hl = md.h * l2e, sqhl = md.sqh * l2e, dl = md.dl, inv_dl = md.inv_dl;
     uint32_t u0, u1;
@@ -103,189 +84,130 @@ __global__ void __launch_bounds__(128, NF <= 40 ? 4 : 2) lmm_adjoint_kernel(cons
             if (!__any_sync(0xffffffffu, active)) break;
             PathGen<SEQ> pg;
             pg.init(gv, active ? i : 0u);
-            float X[NF];
-#pragma unroll
-            for (int k = 0; k < NF; ++k) X[k] = md.X0[k];
-            float *st = sc.store + gt;
+            for (int n = 0; n < nf; ++n) xs[n * bd] = md.X0[n];
+            // records, in float4 units: per step a header (X of the fixed forward, the step's
+            // prefix total A) and the a_n of chunks t/4 .. nch-1 (absolute slots, dead slots 0)
+            float4 *__restrict__ rec = reinterpret_cast<float4 *>(sc.store) + gt;
             // ---------------- forward sweep
             float disc = md.disc0, value = 0.0f;
-            const int nblk = (nf + 7) >> 3;
-            for (int b = 0; b < nblk; ++b) {
-                const int ngrp = (nf - 8 * b + 7) >> 3;
-                const float4 *cb = cst + 8 * b;
-                const float *ccb = ccs + 8 * b;
-                const int nst = min(8, nf - 8 * b);
-                for (int tp = 0; tp < nst; ++tp) {
-                    const int t = 8 * b + tp;
-                    float Az[D], A[D];
+            for (int t = 0; t < nf; ++t) {
+                float Az[D], A[D];
 #pragma unroll
-                    for (int f = 0; f < D; ++f) {
-                        Az[f] = sqhl * Draw<float>::normal(pg, t * D + f);
-                        A[f] = 0.0f;
-                    }
-                    float Xpre = X[0];
-                    switch (tp) {
-#define RQMC_XP(k) \
-    case (k):      \
-        Xpre = X[(k)]; \
-        break;
-                        RQMC_XP(1) RQMC_XP(2) RQMC_XP(3) RQMC_XP(4) RQMC_XP(5) RQMC_XP(6) RQMC_XP(7)
-#undef RQMC_XP
-                        default:
-                            break;
-                    }
-                    *st = Xpre;
-                    st += T;
-                    switch (tp) {
-#define RQMC_G0(k)                                                                          \
-    case (k):                                                                               \
-        adj_fwd_update<D>(X[(k)], lds4(cb + (k)), ccb[(k)], A, Az, hl, st, T);
-                        RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
-#undef RQMC_G0
-                        default:
-                            break;
-                    }
+                for (int f = 0; f < D; ++f) {
+                    Az[f] = sqhl * Draw<float>::normal(pg, t * D + f);
+                    A[f] = 0.0f;
+                }
+                const float Xpre = xs[t * bd];
+                float4 *hdr = rec;
+                rec += T;
+                for (int c = t >> 2; c < nch; ++c) {
+                    float av[4];
 #pragma unroll
-                    for (int gi = 1; gi < NF / 8; ++gi) {
-                        if (gi < ngrp) {
-#pragma unroll
-                            for (int k = 0; k < 8; ++k)
-                                adj_fwd_update<D>(X[8 * gi + k], lds4(cb + 8 * gi + k), ccb[8 * gi + k], A, Az, hl, st, T);
+                    for (int j = 0; j < 4; ++j) {
+                        const int n = 4 * c + j;
+                        av[j] = 0.0f;
+                        if (n >= t && n < nf) {
+                            const float4 cn = cst[n];
+                            const float X = xs[n * bd];
+                            const float a = rcp_approx(1.0f + ex2_approx(-X));
+                            av[j] = a;
+                            A[0] = fmaf(cn.x, a, A[0]);
+                            float inc = fmaf(cn.x, fmaf(A[0], hl, Az[0]), ccs[n]);
+                            if constexpr (D == 2) {
+                                A[1] = fmaf(cn.y, a, A[1]);
+                                inc = fmaf(cn.y, fmaf(A[1], hl, Az[1]), inc);
+                            }
+                            xs[n * bd] = X + inc;
                         }
                     }
-                    float Y = X[0];
-                    switch (tp) {
-#define RQMC_PK(k) \
-    case (k):      \
-        Y = X[(k)]; \
-        break;
-                        RQMC_PK(1) RQMC_PK(2) RQMC_PK(3) RQMC_PK(4) RQMC_PK(5) RQMC_PK(6) RQMC_PK(7)
-#undef RQMC_PK
-                        default:
-                            break;
-                    }
-                    const float e = ex2_approx(Y);
-                    disc *= rcp_approx(1.0f + e);
-                    const float L = e * inv_dl;
-                    float pn = 0.0f;
-                    float *pr = acc + (size_t)(1 + 2 * NF + t * nK) * T;   // unweighted caplet prices
-                    for (int kk = 0; kk < nK; ++kk) {
-                        const float x = L - md.K[kk];
-                        const float c = x > 0.0f ? dl * x * disc : 0.0f;
-                        pn = fmaf(md.w[t][kk], c, pn);
-                        if (active) pr[(size_t)kk * T] += c;
-                    }
-                    value += pn;
+                    *rec = make_float4(av[0], av[1], av[2], av[3]);
+                    rec += T;
                 }
-#pragma unroll
-                for (int k = 0; k + 8 < NF; ++k) X[k] = X[k + 8];
+                *hdr = make_float4(Xpre, A[0], D == 2 ? A[1] : 0.0f, 0.0f);
+                const float e = ex2_approx(xs[t * bd]);
+                disc *= rcp_approx(1.0f + e);
+                const float L = e * inv_dl;
+                float pn = 0.0f;
+                float *pr = accs + (size_t)(1 + NF + t * nK) * T;   // unweighted caplet prices
+                for (int kk = 0; kk < nK; ++kk) {
+                    const float x = L - md.K[kk];
+                    const float cpl = x > 0.0f ? dl * x * disc : 0.0f;
+                    pn = fmaf(md.w[t][kk], cpl, pn);
+                    if (active) pr[(size_t)kk * T] += cpl;
+                }
+                value += pn;
             }
-            // ---------------- reverse sweep (X now holds the adjoints Xb); skipped for zero weights
+            // ---------------- reverse sweep (xs now holds the adjoints Xb); skipped for zero weights
+            for (int n = 0; n < nf; ++n) xs[n * bd] = 0.0f;
             float Dcur = disc, G = 0.0f;
-            const int nblk_rev = md.reverse ? nblk : 0;
+            for (int t = md.reverse ? nf - 1 : -1; t >= 0; --t) {
+                const int c0 = t >> 2;
+                rec -= (size_t)(1 + nch - c0) * T;
+                const float4 h4 = rec[0];
+                const float4 *__restrict__ ch = rec + T;      // chunk c at ch[(c - c0) T]
+                float Ar[D], Zs[D];
+                Ar[0] = h4.y;
+                if constexpr (D == 2) Ar[1] = h4.z;
 #pragma unroll
-            for (int k = 0; k < NF; ++k) X[k] = 0.0f;
-            for (int b = nblk_rev - 1; b >= 0; --b) {
-                if (b != nblk - 1) {
-#pragma unroll
-                    for (int k = NF - 1; k >= 8; --k) X[k] = X[k - 8];
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) X[k] = 0.0f;
+                for (int f = 0; f < D; ++f) Zs[f] = Draw<float>::normal(pg, t * D + f);
+                // post-step value of the fixed forward, with the forward sweep's operations
+                const float4 ct = cst[t];
+                const float4 ac = ch[0];
+                const float a0 = (t & 3) == 0 ? ac.x : (t & 3) == 1 ? ac.y : (t & 3) == 2 ? ac.z : ac.w;
+                float inc = fmaf(ct.x, fmaf(fmaf(ct.x, a0, 0.0f), hl, sqhl * Zs[0]), ccs[t]);
+                if constexpr (D == 2) inc = fmaf(ct.y, fmaf(fmaf(ct.y, a0, 0.0f), hl, sqhl * Zs[1]), inc);
+                const float Y = h4.x + inc;
+                const float e = ex2_approx(Y);
+                const float aY = e * rcp_approx(1.0f + e);
+                const float L = e * inv_dl;
+                float pn = 0.0f, dpn = 0.0f;   // sum w (L-K)^+ and sum w 1{L > K}
+                for (int kk = 0; kk < nK; ++kk) {
+                    const float x = L - md.K[kk];
+                    if (x > 0.0f) {
+                        pn = fmaf(md.w[t][kk], x, pn);
+                        dpn += md.w[t][kk];
+                    }
                 }
-                const int ngrp = (nf - 8 * b + 7) >> 3;
-                const float4 *cb = cst + 8 * b;
-                const float *ccb = ccs + 8 * b;
-                float *vg = acc + (size_t)(1 + NF + 8 * b) * T;   // vega column of original slot 8b
-                const int nst = min(8, nf - 8 * b);
-                for (int tp = nst - 1; tp >= 0; --tp) {
-                    const int t = 8 * b + tp;
-                    const int cnt = 8 * ngrp - tp;                // a-values stored at this step
-                    st -= (size_t)(cnt + 1) * T;
-                    const float Xpre = *st;
-                    const float *sa = st + T;                     // a of shifted slot tp + q at sa[q T]
-                    float Zs[D];
+                G = fmaf(pn * dl, Dcur, G);
+                // an inactive lane (past N) follows a dummy path with zero adjoint source
+                xs[t * bd] += active ? ln2 * (dpn * dl * Dcur * L - aY * G) : 0.0f;
+                Dcur *= 1.0f + e;                             // D_{n-1} = D_n (1 + delta L_n)
+                float B[D];
 #pragma unroll
-                    for (int f = 0; f < D; ++f) Zs[f] = Draw<float>::normal(pg, t * D + f);
-                    // prefix total A over the updated slots
-                    float Atot[D];
+                for (int f = 0; f < D; ++f) B[f] = 0.0f;
+                for (int c = nch - 1; c >= c0; --c) {
+                    const float4 a4 = ch[(size_t)(c - c0) * T];
+                    float4 *vp = vega4 + (size_t)c * T;
+                    float4 v4 = *vp;
+                    const float aa[4] = {a4.x, a4.y, a4.z, a4.w};
+                    float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
-                    for (int f = 0; f < D; ++f) Atot[f] = 0.0f;
-                    for (int q = 0; q < cnt; ++q) {
-                        const float a = sa[(size_t)q * T];
-                        const float4 c = lds4(cb + tp + q);
-                        Atot[0] = fmaf(c.x, a, Atot[0]);
-                        if constexpr (D == 2) Atot[1] = fmaf(c.y, a, Atot[1]);
-                    }
-                    // post-step value of the fixed forward (slot tp, first in the prefix),
-                    // with the forward sweep's exact operations
-                    const float4 c0 = lds4(cb + tp);
-                    const float a0 = sa[0];
-                    float inc = fmaf(c0.x, fmaf(fmaf(c0.x, a0, 0.0f), hl, sqhl * Zs[0]), ccb[tp]);
-                    if constexpr (D == 2) inc = fmaf(c0.y, fmaf(fmaf(c0.y, a0, 0.0f), hl, sqhl * Zs[1]), inc);
-                    const float Y = Xpre + inc;
-                    const float e = ex2_approx(Y);
-                    const float aY = e * rcp_approx(1.0f + e);
-                    const float L = e * inv_dl;
-                    float pn = 0.0f, dpn = 0.0f;   // sum w (L-K)^+ and sum w 1{L > K}, times delta below
-                    for (int kk = 0; kk < nK; ++kk) {
-                        const float x = L - md.K[kk];
-                        if (x > 0.0f) {
-                            pn = fmaf(md.w[t][kk], x, pn);
-                            dpn += md.w[t][kk];
+                    for (int j = 3; j >= 0; --j) {
+                        const int n = 4 * c + j;
+                        if (n >= t && n < nf) {
+                            const float a = aa[j];
+                            const float4 cn = cst[n];
+                            const float Xb = xs[n * bd];
+                            B[0] = fmaf(Xb, cn.x, B[0]);
+                            float sB = cn.x * B[0];
+                            float v = cn.z * l2e * fmaf(Xb, fmaf(md.h, Ar[0] - cn.x, md.sqh * Zs[0]), md.h * a * B[0]);
+                            Ar[0] = fmaf(-cn.x, a, Ar[0]);
+                            if constexpr (D == 2) {
+                                B[1] = fmaf(Xb, cn.y, B[1]);
+                                sB = fmaf(cn.y, B[1], sB);
+                                v = fmaf(cn.w * l2e, fmaf(Xb, fmaf(md.h, Ar[1] - cn.y, md.sqh * Zs[1]), md.h * a * B[1]), v);
+                                Ar[1] = fmaf(-cn.y, a, Ar[1]);
+                            }
+                            vv[j] += v;
+                            xs[n * bd] = fmaf(md.h * sB, a * (1.0f - a), Xb);
                         }
                     }
-                    dpn *= dl;
-                    G = fmaf(pn * dl, Dcur, G);
-                    // an inactive lane (past N) follows a dummy path with zero adjoint source
-                    const float ybar = active ? ln2 * (dpn * Dcur * L - aY * G) : 0.0f;
-                    Dcur *= 1.0f + e;                             // D_{n-1} = D_n (1 + delta L_n)
-                    // back through the step, slots from the last updated down to tp
-                    float B[D], Ar[D];
-#pragma unroll
-                    for (int f = 0; f < D; ++f) {
-                        B[f] = 0.0f;
-                        Ar[f] = Atot[f];
-                    }
-                    auto back = [&](float &Xb, int q) {
-                        const float a = sa[(size_t)q * T];
-                        const float4 c = lds4(cb + tp + q);
-                        B[0] = fmaf(Xb, c.x, B[0]);
-                        float sB = c.x * B[0];
-                        float sbar0 = l2e * fmaf(Xb, fmaf(md.h, Ar[0] - c.x, md.sqh * Zs[0]), md.h * a * B[0]);
-                        float v = sbar0 * c.z;
-                        Ar[0] = fmaf(-c.x, a, Ar[0]);
-                        if constexpr (D == 2) {
-                            B[1] = fmaf(Xb, c.y, B[1]);
-                            sB = fmaf(c.y, B[1], sB);
-                            const float sbar1 =
-                                l2e * fmaf(Xb, fmaf(md.h, Ar[1] - c.y, md.sqh * Zs[1]), md.h * a * B[1]);
-                            v = fmaf(sbar1, c.w, v);
-                            Ar[1] = fmaf(-c.y, a, Ar[1]);
-                        }
-                        float *vq = vg + (size_t)(tp + q) * T;
-                        *vq += v;
-                        Xb = fmaf(md.h * sB, a * (1.0f - a), Xb);
-                    };
-#pragma unroll
-                    for (int gi = NF / 8 - 1; gi >= 1; --gi) {
-                        if (gi < ngrp) {
-#pragma unroll
-                            for (int k = 7; k >= 0; --k) back(X[8 * gi + k], 8 * gi + k - tp);
-                        }
-                    }
-#pragma unroll
-                    for (int k = 7; k >= 0; --k) {
-                        if (k < tp) break;
-                        if (k == tp) X[k] += ybar;                 // payoff adjoint of the fixed forward
-                        back(X[k], k - tp);
-                    }
+                    *vp = make_float4(vv[0], vv[1], vv[2], vv[3]);
                 }
             }
             if (active) {
-                acc[0] += value;
-#pragma unroll
-                for (int k = 0; k < NF; ++k)
-                    if (k < nf) acc[(size_t)(1 + k) * T] += X[k] * md.invL0ln2[k];
+                accs[0] += value;
+                for (int n = 0; n < nf; ++n) accs[(size_t)(1 + n) * T] += xs[n * bd] * md.invL0ln2[n];
             }
         }
         // ---------------- unit flush: sum the CTA's columns in double
@@ -294,12 +216,20 @@ __global__ void __launch_bounds__(128, NF <= 40 ? 4 : 2) lmm_adjoint_kernel(cons
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
         const uint32_t col0 = blockIdx.x * blockDim.x;
         for (int rw = warp; rw < nrow; rw += nw) {
-            const int row = rw == 0 ? 0 : rw <= nf ? rw : rw <= 2 * nf ? 1 + NF + (rw - 1 - nf) : 1 + 2 * NF + (rw - 1 - 2 * nf);
-            float *p = sc.acc + (size_t)row * T + col0;
+            // output row rw: value, delta_n, vega_n, prices; columns of this CTA's threads
+            float *p;
+            int cs;   // float stride between consecutive threads
+            if (rw == 0) { p = sc.acc + (size_t)NF * T + col0; cs = 1; }
+            else if (rw <= nf) { p = sc.acc + (size_t)(NF + rw) * T + col0; cs = 1; }
+            else if (rw <= 2 * nf) {
+                const int n = rw - 1 - nf;
+                p = sc.acc + ((size_t)(n >> 2) * T + col0) * 4 + (n & 3);
+                cs = 4;
+            } else { p = sc.acc + (size_t)(NF + 1 + NF + (rw - 1 - 2 * nf)) * T + col0; cs = 1; }
             double s = 0.0;
             for (int c = lane; c < (int)blockDim.x; c += 32) {
-                s += (double)p[c];
-                p[c] = 0.0f;
+                s += (double)p[(size_t)c * cs];
+                p[(size_t)c * cs] = 0.0f;
             }
             s = warp_sum(s);
             if (lane == 0) r.partials[(size_t)u * nrow + rw] = s;
@@ -315,8 +245,8 @@ namespace rqmc {
 template <int NF, int D, int SEQ>
 static cudaError_t launch_adj_t(const Plan &pl, cudaStream_t st) {
     auto kern = lmm_adjoint_kernel<NF, D, SEQ>;
-    size_t a, b;
-    const size_t smem = adj_smem_layout<NF>(pl.gen, &a, &b);
+    size_t a, b, c;
+    const size_t smem = adj_smem_layout<NF>(pl.gen, pl.threads, &a, &b, &c);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -328,8 +258,8 @@ static cudaError_t launch_adj_t(const Plan &pl, cudaStream_t st) {
 template <int NF, int D, int SEQ>
 static int grid_adj_t(const Plan &pl) {
     auto kern = lmm_adjoint_kernel<NF, D, SEQ>;
-    size_t a, b;
-    const size_t smem = adj_smem_layout<NF>(pl.gen, &a, &b);
+    size_t a, b, c;
+    const size_t smem = adj_smem_layout<NF>(pl.gen, pl.threads, &a, &b, &c);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);

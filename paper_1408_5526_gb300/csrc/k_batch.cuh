@@ -43,9 +43,10 @@ __device__ __forceinline__ void batch_lmm(const BatchInst &bi, const BatchItem &
         const uint32_t i = it.tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
         const bool active = i < r.N;
         if (!__any_sync(0xffffffffu, active)) break;
-        PathGen<SEQ> pg;
-        pg.init(gv, active ? i : 0u);
-        lmm_path<NF, SEQ, float>(pg, active, sc, cst, X0, Ks, zb, wbuf, acc + warp * nout, cmp + warp * nout, lane);
+        PathGen<SEQ> pg[1];
+        pg[0].init(gv, active ? i : 0u);
+        const bool act[1] = {active};
+        lmm_path<NF, SEQ, float, 1>(pg, act, sc, cst, X0, Ks, zb, wbuf, acc + warp * nout, cmp + warp * nout, lane);
     }
     flush_unit(r, it.m * bi.tiles_per_m + it.tile, acc, cmp);
 }

@@ -87,7 +87,7 @@ struct LmmScal {
 
 // Shared memory: [generator stage][(sigma, cc) x NF][X0 x NF, K x 8][normals 8 x threads]
 //                [transpose buffers][acc][cmp]
-template <int NF, typename T>
+template <int NF, typename T, int P = 1>
 __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, int nw, int nK, int nout,
                                                            size_t *o_cst, size_t *o_x0, size_t *o_z, size_t *o_buf,
                                                            size_t *o_acc) {
@@ -97,7 +97,7 @@ __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, i
     *o_x0 = off;
     off = align16(off + sizeof(T) * (NF + kMaxStrikes));
     *o_z = off;
-    off = align16(off + sizeof(T) * 8 * 32 * (size_t)nw);
+    off = align16(off + sizeof(T) * 8 * P * 32 * (size_t)nw);
     *o_buf = off;
     off = align16(off + sizeof(T) * (size_t)nw * 8 * nK * LmmMath<T>::PAD);
     *o_acc = off;
@@ -110,15 +110,19 @@ __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, i
 #define RQMC_LMM_EXTRA_REGS 44
 #endif
 template <int NF, typename T>
+constexpr int lmm_ilp();
+template <int NF, typename T>
 constexpr int lmm_min_blocks() {
-    constexpr int regs = (int)(NF * sizeof(T) / 4) + RQMC_LMM_EXTRA_REGS;
+    constexpr int regs = (int)(NF * sizeof(T) / 4) * lmm_ilp<NF, T>() + RQMC_LMM_EXTRA_REGS;
     return regs <= 64 ? 4 : regs <= 85 ? 3 : regs <= 128 ? 2 : 1;
 }
 
-// One path: forwards in registers, per-step payoffs into the warp's transpose buffer,
-// block sums into the warp's Kahan accumulators (wacc/wcmp, indexed by output t nK + k).
-template <int NF, int SEQ, typename T>
-__device__ __forceinline__ void lmm_path(PathGen<SEQ> &pg, const bool active, const LmmScal<T> &sc,
+// P paths in lockstep (P = 1 or 2): forwards in registers, per-step payoffs (summed over
+// the P paths) into the warp's transpose buffer, block sums into the warp's Kahan
+// accumulators (wacc/wcmp, indexed by output t nK + k).  The P paths share every constant
+// load and all control flow, and give each warp P independent dependency chains.
+template <int NF, int SEQ, typename T, int P>
+__device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&active)[P], const LmmScal<T> &sc,
                                          const typename LmmMath<T>::V2 *cst, const T *X0, const T *Ks, T *zb,
                                          T *wbuf, T *wacc, T *wcmp, const int lane) {
     using M = LmmMath<T>;
@@ -126,26 +130,42 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> &pg, const bool active, co
     constexpr int PAD = M::PAD;
     const int nf = sc.nf, nK = sc.nK;
     const T hc = sc.hc, sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
-    T X[NF];
+    const int zs = P * blockDim.x;   // stride of one step in the normals buffer
+    T X[P][NF];
 #pragma unroll
-    for (int k = 0; k < NF; ++k) X[k] = X0[k];
-    T disc = sc.disc0;
+    for (int k = 0; k < NF; ++k) {
+        const T x0 = X0[k];
+#pragma unroll
+        for (int p = 0; p < P; ++p) X[p][k] = x0;
+    }
+    T disc[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) disc[p] = sc.disc0;
     const int nblk = (nf + 7) >> 3;
     for (int b = 0; b < nblk; ++b) {
         const int ngrp = (nf - 8 * b + 7) >> 3;   // groups of 8 shifted slots still alive
         const V2 *cb = cst + 8 * b;               // constants of original slot 8b + k
         const int nst = min(8, nf - 8 * b);
         // phase A: the block's normals (one short generator loop)
-        for (int tp = 0; tp < nst; ++tp) zb[tp * blockDim.x] = Draw<T>::normal(pg, 8 * b + tp);
-        // phase B: forward updates and payoffs (each thread reads back its own column)
         for (int tp = 0; tp < nst; ++tp) {
-            const T Az = sqhc * zb[tp * blockDim.x];
-            T S = T(0);
+#pragma unroll
+            for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = Draw<T>::normal(pg[p], 8 * b + tp);
+        }
+        // phase B: forward updates and payoffs (each thread reads back its own columns)
+        for (int tp = 0; tp < nst; ++tp) {
+            T Az[P], S[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                Az[p] = sqhc * zb[tp * zs + p * blockDim.x];
+                S[p] = T(0);
+            }
             // group 0: alive slots tp..7, entered through a fall-through switch
             switch (tp) {
-#define RQMC_G0(k)                                                   \
-    case (k):                                                        \
-        lmm_update<T>(X[(k)], M::lds(cb + (k)), S, hc, Az);
+#define RQMC_G0(k)                                                                    \
+    case (k): {                                                                       \
+        const V2 c = M::lds(cb + (k));                                                \
+        _Pragma("unroll") for (int p = 0; p < P; ++p) lmm_update<T>(X[p][(k)], c, S[p], hc, Az[p]); \
+    }
                 RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
 #undef RQMC_G0
                 default:
@@ -155,28 +175,45 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> &pg, const bool active, co
             for (int gi = 1; gi < NF / 8; ++gi) {
                 if (gi < ngrp) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) lmm_update<T>(X[8 * gi + k], M::lds(cb + 8 * gi + k), S, hc, Az);
+                    for (int k = 0; k < 8; ++k) {
+                        const V2 c = M::lds(cb + 8 * gi + k);
+#pragma unroll
+                        for (int p = 0; p < P; ++p) lmm_update<T>(X[p][8 * gi + k], c, S[p], hc, Az[p]);
+                    }
                 }
             }
             // L_{t+1}(T_{t+1}) = b^X / delta sits in shifted slot tp
-            T Xf = X[0];
+            T Xf[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) Xf[p] = X[p][0];
             switch (tp) {
-#define RQMC_PK(k) \
-    case (k):      \
-        Xf = X[(k)]; \
+#define RQMC_PK(k)                                                       \
+    case (k):                                                            \
+        _Pragma("unroll") for (int p = 0; p < P; ++p) Xf[p] = X[p][(k)]; \
         break;
                 RQMC_PK(1) RQMC_PK(2) RQMC_PK(3) RQMC_PK(4) RQMC_PK(5) RQMC_PK(6) RQMC_PK(7)
 #undef RQMC_PK
                 default:
                     break;
             }
-            const T e = M::expb(Xf);
-            disc *= M::rcp(T(1) + e);
-            const T Lf = e * inv_dl, dd = dl * disc;
+            T Lf[P], dd[P];
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const T e = M::expb(Xf[p]);
+                disc[p] *= M::rcp(T(1) + e);
+                Lf[p] = e * inv_dl;
+                dd[p] = active[p] ? dl * disc[p] : T(0);
+            }
             T *row = wbuf + (size_t)tp * nK * PAD + lane;
             for (int kk = 0; kk < nK; ++kk) {
-                const T x = Lf - Ks[kk];
-                row[kk * PAD] = (active && x > T(0)) ? x * dd : T(0);
+                const T K = Ks[kk];
+                T pay = T(0);
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    const T x = Lf[p] - K;
+                    pay += x > T(0) ? x * dd[p] : T(0);
+                }
+                row[kk * PAD] = pay;
             }
         }
         __syncwarp();
@@ -192,8 +229,21 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> &pg, const bool active, co
         }
         __syncwarp();
 #pragma unroll
-        for (int k = 0; k + 8 < NF; ++k) X[k] = X[k + 8];
+        for (int k = 0; k + 8 < NF; ++k) {
+#pragma unroll
+            for (int p = 0; p < P; ++p) X[p][k] = X[p][k + 8];
+        }
     }
+}
+
+// Paths per thread in lockstep for a bucket: two where the registers allow it.
+template <int NF, typename T>
+constexpr int lmm_ilp() {
+#ifdef RQMC_LMM_ILP
+    return (NF * (int)sizeof(T) / 4) <= 40 ? RQMC_LMM_ILP : 1;
+#else
+    return (NF * (int)sizeof(T) / 4) <= 40 ? 2 : 1;
+#endif
 }
 
 template <int NF, int SEQ, typename T>
@@ -204,9 +254,10 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nK = md.nK, nout = r.nout;
+    constexpr int P = lmm_ilp<NF, T>();
     size_t o_cst, o_x0, o_z, o_buf, o_acc;
-    lmm_smem_layout<NF, T>(g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
-    T *zb = reinterpret_cast<T *>(smem_raw + o_z) + threadIdx.x;   // [8][blockDim], own column
+    lmm_smem_layout<NF, T, P>(g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
+    T *zb = reinterpret_cast<T *>(smem_raw + o_z) + threadIdx.x;   // [8][P][blockDim], own columns
     V2 *cst = reinterpret_cast<V2 *>(smem_raw + o_cst);
     T *X0 = reinterpret_cast<T *>(smem_raw + o_x0);
     T *Ks = X0 + NF;
@@ -234,13 +285,19 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
             staged_m = m;
         }
         __syncthreads();
-        for (int pp = 0; pp < r.ppt; ++pp) {
-            const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
-            const bool active = i < r.N;
-            if (!__any_sync(0xffffffffu, active)) break;
-            PathGen<SEQ> pg;
-            pg.init(gv, active ? i : 0u);
-            lmm_path<NF, SEQ, T>(pg, active, sc, cst, X0, Ks, zb, wbuf, wacc, wcmp, lane);
+        for (int pp = 0; pp < r.ppt; pp += P) {
+            PathGen<SEQ> pg[P];
+            bool active[P];
+            bool any = false;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const uint32_t i = tile * r.tile + (uint32_t)((pp + p) * blockDim.x + threadIdx.x);
+                active[p] = pp + p < r.ppt && i < r.N;
+                any = any || active[p];
+                pg[p].init(gv, active[p] ? i : 0u);
+            }
+            if (!__any_sync(0xffffffffu, any)) break;
+            lmm_path<NF, SEQ, T, P>(pg, active, sc, cst, X0, Ks, zb, wbuf, wacc, wcmp, lane);
         }
         flush_unit(r, u, acc, cmp);
     }
@@ -251,7 +308,8 @@ static cudaError_t launch_lmm_t(const Plan &pl, const LmmModel<T> &md, cudaStrea
     auto kern = lmm_caplet_kernel<NF, SEQ, T>;
     const int threads = pl.threads;
     size_t a, b, c, d, e2;
-    const size_t smem = lmm_smem_layout<NF, T>(pl.gen, threads / 32, md.nK, pl.red.nout, &a, &b, &c, &d, &e2);
+    const size_t smem =
+        lmm_smem_layout<NF, T, lmm_ilp<NF, T>()>(pl.gen, threads / 32, md.nK, pl.red.nout, &a, &b, &c, &d, &e2);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

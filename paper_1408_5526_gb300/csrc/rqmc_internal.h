@@ -89,8 +89,8 @@ struct AdjModel {
 
 // Per-thread global columns of the adjoint kernel (column stride T = threads in the grid).
 struct AdjScratch {
-    float *store;   // forward-sweep records: per step the fixed forward's pre-step X, then the a_n
-    float *acc;     // [1 + 2 NF + nf nK] rows: value, dV/dL_n(0), dV/dvol_n, caplet prices
+    float *store;   // forward-sweep records, float4 chunks interleaved by thread
+    float *acc;     // vega as float4 chunks [NF/4][T], then value, dV/dL_n(0) [NF], caplet prices [nf nK]
     uint32_t T;
 };
 
