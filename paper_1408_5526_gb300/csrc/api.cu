@@ -542,6 +542,16 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
     md->reverse = any_w ? 1 : 0;
     rs = finish_plan(pl, {}, 16, (size_t)pl->red.units * nout, 0, nullptr);
     if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
+    // CTA size: the one with more resident warps per SM (each thread's state column in shared
+    // memory competes with the staged generator tables)
+    int best = 0, best_th = 128;
+    for (int th : {128, 256}) {
+        pl->threads = th;
+        const int w = adjoint_occupancy(*pl) * th;
+        if (w > best) { best = w; best_th = th; }
+    }
+    if (best == 0) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
+    set_reduction(*pl, nout, best_th, 4);
     pl->grid = adjoint_grid(*pl);
     if (pl->grid < 1) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
     // per-thread records (float4 units): per step t a header and chunks t/4 .. ceil(nf/4)-1

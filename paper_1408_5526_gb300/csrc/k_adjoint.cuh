@@ -43,8 +43,15 @@ __host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, i
     return off;
 }
 
+// Resident CTAs per SM that the register budget must allow: the shared-memory state columns
+// limit residency to 2 CTAs of 256 threads (4 of 128) for the staged sequences anyway, so up
+// to 128 registers cost no occupancy and let the unrolled chunk code keep its loads in flight.
+#ifndef RQMC_ADJ_MIN_BLOCKS
+#define RQMC_ADJ_MIN_BLOCKS 2
+#endif
+
 template <int NF, int D, int SEQ>
-__global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, const AdjModel md, const AdjScratch sc,
+__global__ void __launch_bounds__(256, RQMC_ADJ_MIN_BLOCKS) lmm_adjoint_kernel(const GenParams g, const AdjModel md, const AdjScratch sc,
                                                          const RedParams r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     size_t o_cst, o_cc, o_st;
@@ -84,7 +91,9 @@ __global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, con
             if (!__any_sync(0xffffffffu, active)) break;
             PathGen<SEQ> pg;
             pg.init(gv, active ? i : 0u);
-            for (int n = 0; n < nf; ++n) xs[n * bd] = md.X0[n];
+            // slots nf .. 4 nch - 1 are padding with zero volatility: they stay constant and feed
+            // nothing into the drifts, the adjoints or the vegas, so full chunks need no checks
+            for (int n = 0; n < 4 * nch; ++n) xs[n * bd] = md.X0[n];
             // records, in float4 units: per step a header (X of the fixed forward, the step's
             // prefix total A) and the a_n of chunks t/4 .. nch-1 (absolute slots, dead slots 0)
             float4 *__restrict__ rec = reinterpret_cast<float4 *>(sc.store) + gt;
@@ -100,13 +109,14 @@ __global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, con
                 const float Xpre = xs[t * bd];
                 float4 *hdr = rec;
                 rec += T;
-                for (int c = t >> 2; c < nch; ++c) {
+                // one chunk of four slots, slots below jlo are fixed forwards (a = 0)
+                auto fwd_chunk = [&](int c, int jlo) {
                     float av[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const int n = 4 * c + j;
                         av[j] = 0.0f;
-                        if (n >= t && n < nf) {
+                        if (j >= jlo) {
                             const float4 cn = cst[n];
                             const float X = xs[n * bd];
                             const float a = rcp_approx(1.0f + ex2_approx(-X));
@@ -122,7 +132,9 @@ __global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, con
                     }
                     *rec = make_float4(av[0], av[1], av[2], av[3]);
                     rec += T;
-                }
+                };
+                fwd_chunk(t >> 2, t & 3);
+                for (int c = (t >> 2) + 1; c < nch; ++c) fwd_chunk(c, 0);
                 *hdr = make_float4(Xpre, A[0], D == 2 ? A[1] : 0.0f, 0.0f);
                 const float e = ex2_approx(xs[t * bd]);
                 disc *= rcp_approx(1.0f + e);
@@ -133,18 +145,21 @@ __global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, con
                     const float x = L - md.K[kk];
                     const float cpl = x > 0.0f ? dl * x * disc : 0.0f;
                     pn = fmaf(md.w[t][kk], cpl, pn);
-                    if (active) pr[(size_t)kk * T] += cpl;
+                    if (active) atomicAdd(pr + (size_t)kk * T, cpl);   // own column: a plain reduction
                 }
                 value += pn;
             }
             // ---------------- reverse sweep (xs now holds the adjoints Xb); skipped for zero weights
-            for (int n = 0; n < nf; ++n) xs[n * bd] = 0.0f;
+            for (int n = 0; n < 4 * nch; ++n) xs[n * bd] = 0.0f;
             float Dcur = disc, G = 0.0f;
             for (int t = md.reverse ? nf - 1 : -1; t >= 0; --t) {
                 const int c0 = t >> 2;
                 rec -= (size_t)(1 + nch - c0) * T;
                 const float4 h4 = rec[0];
                 const float4 *__restrict__ ch = rec + T;      // chunk c at ch[(c - c0) T]
+                // software pipeline: the next chunk's a_n and vega are loaded one chunk ahead
+                float4 a4n = ch[(size_t)(nch - 1 - c0) * T];
+                float4 v4n = vega4[(size_t)(nch - 1) * T];
                 float Ar[D], Zs[D];
                 Ar[0] = h4.y;
                 if constexpr (D == 2) Ar[1] = h4.z;
@@ -175,16 +190,13 @@ __global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, con
                 float B[D];
 #pragma unroll
                 for (int f = 0; f < D; ++f) B[f] = 0.0f;
-                for (int c = nch - 1; c >= c0; --c) {
-                    const float4 a4 = ch[(size_t)(c - c0) * T];
-                    float4 *vp = vega4 + (size_t)c * T;
-                    float4 v4 = *vp;
+                auto rev_chunk = [&](int c, int jlo, const float4 a4, const float4 v4) {
                     const float aa[4] = {a4.x, a4.y, a4.z, a4.w};
                     float vv[4] = {v4.x, v4.y, v4.z, v4.w};
 #pragma unroll
                     for (int j = 3; j >= 0; --j) {
                         const int n = 4 * c + j;
-                        if (n >= t && n < nf) {
+                        if (j >= jlo) {
                             const float a = aa[j];
                             const float4 cn = cst[n];
                             const float Xb = xs[n * bd];
@@ -202,12 +214,19 @@ __global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, con
                             xs[n * bd] = fmaf(md.h * sB, a * (1.0f - a), Xb);
                         }
                     }
-                    *vp = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    vega4[(size_t)c * T] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                };
+                for (int c = nch - 1; c > c0; --c) {
+                    const float4 a4 = a4n, v4 = v4n;
+                    a4n = ch[(size_t)(c - 1 - c0) * T];
+                    v4n = vega4[(size_t)(c - 1) * T];
+                    rev_chunk(c, 0, a4, v4);
                 }
+                rev_chunk(c0, t & 3, a4n, v4n);
             }
             if (active) {
-                accs[0] += value;
-                for (int n = 0; n < nf; ++n) accs[(size_t)(1 + n) * T] += xs[n * bd] * md.invL0ln2[n];
+                atomicAdd(accs, value);
+                for (int n = 0; n < nf; ++n) atomicAdd(accs + (size_t)(1 + n) * T, xs[n * bd] * md.invL0ln2[n]);
             }
         }
         // ---------------- unit flush: sum the CTA's columns in double
@@ -228,7 +247,7 @@ __global__ void __launch_bounds__(128) lmm_adjoint_kernel(const GenParams g, con
             } else { p = sc.acc + (size_t)(NF + 1 + NF + (rw - 1 - 2 * nf)) * T + col0; cs = 1; }
             double s = 0.0;
             for (int c = lane; c < (int)blockDim.x; c += 32) {
-                s += (double)p[(size_t)c * cs];
+                s += (double)__ldcg(p + (size_t)c * cs);   // from L2: the columns were reduced there
                 p[(size_t)c * cs] = 0.0f;
             }
             s = warp_sum(s);
@@ -256,7 +275,7 @@ static cudaError_t launch_adj_t(const Plan &pl, cudaStream_t st) {
 }
 
 template <int NF, int D, int SEQ>
-static int grid_adj_t(const Plan &pl) {
+static int grid_adj_t(const Plan &pl, int mode) {
     auto kern = lmm_adjoint_kernel<NF, D, SEQ>;
     size_t a, b, c;
     const size_t smem = adj_smem_layout<NF>(pl.gen, pl.threads, &a, &b, &c);
@@ -265,19 +284,20 @@ static int grid_adj_t(const Plan &pl) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.threads, smem);
+    if (mode == 2) return occ;
     if (occ < 1) occ = 1;
     return (int)std::min<unsigned long long>(pl.red.units, (unsigned long long)occ * sms);
 }
 
-// mode 0: launch, mode 1: return the persistent grid size
+// mode 0: launch, mode 1: return the persistent grid size, mode 2: resident CTAs per SM
 template <int SEQ>
 int adjoint_seq(const Plan &pl, cudaStream_t st, int mode) {
     const bool two = pl.adjm->d == 2;
     if (pl.nf_bucket == 40) {
-        if (mode) return two ? grid_adj_t<40, 2, SEQ>(pl) : grid_adj_t<40, 1, SEQ>(pl);
+        if (mode) return two ? grid_adj_t<40, 2, SEQ>(pl, mode) : grid_adj_t<40, 1, SEQ>(pl, mode);
         return (int)(two ? launch_adj_t<40, 2, SEQ>(pl, st) : launch_adj_t<40, 1, SEQ>(pl, st));
     }
-    if (mode) return two ? grid_adj_t<80, 2, SEQ>(pl) : grid_adj_t<80, 1, SEQ>(pl);
+    if (mode) return two ? grid_adj_t<80, 2, SEQ>(pl, mode) : grid_adj_t<80, 1, SEQ>(pl, mode);
     return (int)(two ? launch_adj_t<80, 2, SEQ>(pl, st) : launch_adj_t<80, 1, SEQ>(pl, st));
 }
 

@@ -193,6 +193,7 @@ int64_t batch_output_size(const Plan &pl);
 void batch_destroy(Plan &pl);
 int batch_ppt(const Plan &pl);
 int adjoint_grid(const Plan &pl);
+int adjoint_occupancy(const Plan &pl);   // resident CTAs per SM at pl.threads
 int occupancy_blocks(const Plan &pl);
 
 // ---- errors
