@@ -505,7 +505,7 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
     const int nout = 1 + 2 * nf + nf * n_strikes;
     pl->nf_bucket = nf <= 40 ? 40 : 80;
     pl->checkpoint = 1;
-    set_reduction(*pl, nout, 128, 4);
+    set_reduction(*pl, nout, kAdjointThreads, 4);
     AdjModel *md = new AdjModel();
     std::memset(md, 0, sizeof(AdjModel));
     pl->adjm = md;
@@ -542,22 +542,14 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
     md->reverse = any_w ? 1 : 0;
     rs = finish_plan(pl, {}, 16, (size_t)pl->red.units * nout, 0, nullptr);
     if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
-    // CTA size: the one with more resident warps per SM (each thread's state column in shared
-    // memory competes with the staged generator tables)
-    int best = 0, best_th = 128;
-    for (int th : {128, 256}) {
-        pl->threads = th;
-        const int w = adjoint_occupancy(*pl) * th;
-        if (w > best) { best = w; best_th = th; }
-    }
-    if (best == 0) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
-    set_reduction(*pl, nout, best_th, 4);
     pl->grid = adjoint_grid(*pl);
     if (pl->grid < 1) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
     // per-thread records (float4 units): per step t a header and chunks t/4 .. ceil(nf/4)-1
     size_t E = 0;
     for (int t = 0; t < nf; ++t) E += 4 * (size_t)(1 + (nf + 3) / 4 - t / 4);
-    const uint32_t T = (uint32_t)pl->grid * (uint32_t)pl->threads;
+    // column stride: the grid's threads plus 96 unused columns, so consecutive record rows are
+    // not 64 KiB-aligned multiples of each other (fewer DRAM partition conflicts)
+    const uint32_t T = (uint32_t)pl->grid * (uint32_t)pl->threads + 96;
     const size_t rows = 1 + 2 * (size_t)pl->nf_bucket + (size_t)nf * n_strikes;   // vega chunks, value, delta, prices
     pl->adjs.T = T;
     const size_t bytes = sizeof(float) * ((size_t)E + rows) * T;

@@ -18,10 +18,4 @@ int adjoint_grid(const Plan &pl) {
 #undef RQMC_L
 }
 
-int adjoint_occupancy(const Plan &pl) {
-#define RQMC_L(S) adjoint_seq<S>(pl, 0, 2)
-    return RQMC_SEQ_DISPATCH(pl.seq, RQMC_L);
-#undef RQMC_L
-}
-
 }  // namespace rqmc

@@ -2,76 +2,92 @@
 // and the estimator are Sec. 5's), instantiated per sequence by k_adjoint_{halton,sobol,philox}.cu.
 //
 // Objective per path: V = sum_n sum_k w_{n,k} delta (L_n(T_n) - K_k)^+ D_n with the spot
-// numeraire D_n = prod_{j<=n} (1 + delta L_j(T_j))^-1.  Forwards live in registers as
+// numeraire D_n = prod_{j<=n} (1 + delta L_j(T_j))^-1.  Forwards are carried as
 // X_n = log2(delta L_n); one log-Euler step of slot n (d factors) is
 //     a_n = 1 / (1 + 2^-X_n)               (= delta L_n / (1 + delta L_n))
 //     A_n = sum_{j<=n, alive} sigma_j a_j   (d-vector prefix)
 //     X_n += log2 e (h sigma_n.A_n + sqrt(h) sigma_n.Z - h |sigma_n|^2 / 2).
-// Each thread keeps its path's X_n (then the adjoints) in a shared-memory column and loops
-// over the alive forwards with rolled loops, so the code stays small and about 60
-// registers give ~20 warps per SM.  The forward sweep stores, per step, a header (the
-// pre-step X of the forward fixed at that step, the step's prefix total A) and the a_n in
-// 16-byte chunks aligned to absolute forward slots, interleaved by thread in global scratch:
-// one coalesced 128-bit store (and, in the reverse sweep, one 128-bit load) per four
-// forwards.  The vega accumulators use the same chunking.  Reverse sweep: with
-// Xb_n = dV/dX_n in registers and B_n = sum_{m>=n} Xb_m sigma_m,
+// Each thread keeps its path's X_n (then the adjoints) in a shared-memory column with a
+// compile-time stride and loops over the alive forwards four slots (one chunk) at a time.
+// The forward sweep stores, per step, a header (the pre-step X of the forward fixed at that
+// step, the step's prefix total A) and the a_n in 16-byte chunks aligned to absolute forward
+// slots, interleaved by thread in global scratch: one coalesced 128-bit streaming store per
+// four forwards, read back once by the reverse sweep two chunks ahead.  The vega accumulators
+// use the same chunking and are updated by vector reductions that the thread does not wait
+// for.  With Xb_n = dV/dX_n and B_n = sum_{m>=n} Xb_m sigma_m, the reverse sweep of a step
+// visits the alive slots top-down and applies
 //     sigma_bar_n = log2 e [Xb_n (h A_n + sqrt(h) Z - h sigma_n) + h a_n B_n]
 //     Xb_n       += h (sigma_n.B_n) a_n (1 - a_n)
-// and at the fixing of forward n (Y = its post-step X, L = 2^Y / delta, G_n = sum_{m>=n} P_m)
+// (A_n recovered top-down from the stored total), and at the fixing of forward n (Y = its
+// post-step X, L = 2^Y / delta, G_n = sum_{m>=n} P_m)
 //     Xb_n       += ln 2 [sum_k w_{n,k} delta 1{L > K_k} D_n L - a(Y) G_n].
 // The normals of a step are regenerated from the counter, never stored.  At the end
 // dV/dL_n(0) = Xb_n / (L_n(0) ln 2) and dV/dvol_n = sum over steps of sigma_bar_n . b_n.
-// Per-thread value / delta / vega accumulators sit in global columns; each (replication,
-// tile) unit sums its CTA's columns in double into its own partial row.
+// Per-thread value / delta / vega / price accumulators sit in global columns; each
+// (replication, tile) unit sums its CTA's columns in double into its own partial row.
 #pragma once
 #include "paths_common.cuh"
 
 namespace rqmc {
 
-// Shared memory: [generator stage][(sigma_1, sigma_2, b_1, b_2) x NF][cc x NF]
-//                [per-thread state x NF x blockDim]  (forward X, then the adjoints Xb)
+// Fire-and-forget vector reduction into global memory (no value returned, so the issuing
+// thread never waits on it).  Each address is one thread's own column, and reductions from
+// one thread to one address take effect in program order, so the sums are deterministic.
+__device__ __forceinline__ void red_add_v4(float4 *p, const float (&v)[4]) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(v[0]), "f"(v[1]), "f"(v[2]),
+                 "f"(v[3])
+                 : "memory");
+}
+
+// Threads per CTA.  Fixed, so that a thread's state column has a compile-time stride and
+// every shared-memory access of the sweeps is an immediate offset from one pointer.
+constexpr int kAdjThreads = kAdjointThreads;
+
+// Shared memory: [generator stage][forward constants (sigma_1, sigma_2, cc, 0) x NF]
+//                [reverse constants (h sigma_1, h sigma_2, b_1 log2 e, b_2 log2 e) x NF]
+//                [per-thread state x NF x kAdjThreads]  (forward X, then the adjoints Xb)
 template <int NF>
-__host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, int threads, size_t *o_cst,
-                                                           size_t *o_cc, size_t *o_st) {
+__host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, size_t *o_fw, size_t *o_rv,
+                                                           size_t *o_st) {
     size_t off = align16(stage_bytes(g));
-    *o_cst = off;
-    off = align16(off + sizeof(float4) * NF);
-    *o_cc = off;
-    off = align16(off + sizeof(float) * NF);
+    *o_fw = off;
+    off += sizeof(float4) * NF;
+    *o_rv = off;
+    off += sizeof(float4) * NF;
     *o_st = off;
-    off = align16(off + sizeof(float) * NF * (size_t)threads);
+    off = align16(off + sizeof(float) * NF * (size_t)kAdjThreads);
     return off;
 }
 
-// Resident CTAs per SM that the register budget must allow: the shared-memory state columns
-// limit residency to 2 CTAs of 256 threads (4 of 128) for the staged sequences anyway, so up
-// to 128 registers cost no occupancy and let the unrolled chunk code keep its loads in flight.
+// The shared-memory state columns limit residency to 2 CTAs per SM for the staged sequences,
+// so a budget of up to 128 registers costs no occupancy and lets each chunk keep its loads
+// and SFU results in flight.
 #ifndef RQMC_ADJ_MIN_BLOCKS
 #define RQMC_ADJ_MIN_BLOCKS 2
 #endif
 
 template <int NF, int D, int SEQ>
-__global__ void __launch_bounds__(256, RQMC_ADJ_MIN_BLOCKS) lmm_adjoint_kernel(const GenParams g, const AdjModel md, const AdjScratch sc,
-                                                         const RedParams r) {
+__global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
+    lmm_adjoint_kernel(const GenParams g, const AdjModel md, const AdjScratch sc, const RedParams r) {
+    constexpr int BD = kAdjThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    size_t o_cst, o_cc, o_st;
-    adj_smem_layout<NF>(g, blockDim.x, &o_cst, &o_cc, &o_st);
-    float4 *cst = reinterpret_cast<float4 *>(smem_raw + o_cst);
-    float *ccs = reinterpret_cast<float *>(smem_raw + o_cc);
-    float *xs = reinterpret_cast<float *>(smem_raw + o_st) + threadIdx.x;   // slot n at xs[n * blockDim]
-    const int bd = blockDim.x;
-    for (int k = threadIdx.x; k < NF; k += blockDim.x) {
-        cst[k] = make_float4(md.sg[k][0], md.sg[k][1], md.b[k][0], md.b[k][1]);
-        ccs[k] = md.cc[k];
+    size_t o_fw, o_rv, o_st;
+    adj_smem_layout<NF>(g, &o_fw, &o_rv, &o_st);
+    float4 *cfw = reinterpret_cast<float4 *>(smem_raw + o_fw);
+    float4 *crv = reinterpret_cast<float4 *>(smem_raw + o_rv);
+    float *xcol = reinterpret_cast<float *>(smem_raw + o_st) + threadIdx.x;   // slot n at xcol[n BD]
+    const float l2e = 1.4426950408889634f, ln2 = 0.6931471805599453f;
+    for (int k = threadIdx.x; k < NF; k += BD) {
+        cfw[k] = make_float4(md.sg[k][0], md.sg[k][1], md.cc[k], 0.0f);
+        crv[k] = make_float4(md.h * md.sg[k][0], md.h * md.sg[k][1], md.b[k][0] * l2e, md.b[k][1] * l2e);
     }
     const uint32_t T = sc.T;                              // threads in the grid: column stride
-    const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t gt = blockIdx.x * BD + threadIdx.x;
     // accumulators: vega as float4 chunks [NF/4][T], then value [T], delta [NF][T], prices [nf nK][T]
-    float4 *__restrict__ vega4 = reinterpret_cast<float4 *>(sc.acc) + gt;
+    float4 *const vega4 = reinterpret_cast<float4 *>(sc.acc) + gt;
     float *accs = sc.acc + (size_t)NF * T + gt;
     const int nf = md.nf, nK = md.nK, nch = (nf + 3) >> 2;
-    const float l2e = 1.4426950408889634f, ln2 = 0.6931471805599453f;
-    const float hl = md.h * l2e, sqhl = md.sqh * l2e, dl = md.dl, inv_dl = md.inv_dl;
+    const float h = md.h, inv_h = 1.0f / md.h, hl = md.h * l2e, sqhl = md.sqh * l2e, dl = md.dl, inv_dl = md.inv_dl;
     uint32_t u0, u1;
     unit_range(r, u0, u1);
     GenView gv;
@@ -86,57 +102,59 @@ __global__ void __launch_bounds__(256, RQMC_ADJ_MIN_BLOCKS) lmm_adjoint_kernel(c
         }
         __syncthreads();
         for (int pp = 0; pp < r.ppt; ++pp) {
-            const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
+            const uint32_t i = tile * r.tile + (uint32_t)(pp * BD + threadIdx.x);
             const bool active = i < r.N;
             if (!__any_sync(0xffffffffu, active)) break;
             PathGen<SEQ> pg;
             pg.init(gv, active ? i : 0u);
             // slots nf .. 4 nch - 1 are padding with zero volatility: they stay constant and feed
             // nothing into the drifts, the adjoints or the vegas, so full chunks need no checks
-            for (int n = 0; n < 4 * nch; ++n) xs[n * bd] = md.X0[n];
+            for (int n = 0; n < 4 * nch; ++n) xcol[n * BD] = md.X0[n];
             // records, in float4 units: per step a header (X of the fixed forward, the step's
-            // prefix total A) and the a_n of chunks t/4 .. nch-1 (absolute slots, dead slots 0)
-            float4 *__restrict__ rec = reinterpret_cast<float4 *>(sc.store) + gt;
+            // prefix total A) and the a_n of chunks t/4 .. nch-1 (absolute slots, dead slots 0).
+            // Each record is read once, by the reverse sweep: streaming (evict-first) accesses.
+            float4 *rec = reinterpret_cast<float4 *>(sc.store) + gt;
             // ---------------- forward sweep
             float disc = md.disc0, value = 0.0f;
             for (int t = 0; t < nf; ++t) {
-                float Az[D], A[D];
-#pragma unroll
-                for (int f = 0; f < D; ++f) {
-                    Az[f] = sqhl * Draw<float>::normal(pg, t * D + f);
-                    A[f] = 0.0f;
-                }
-                const float Xpre = xs[t * bd];
+                float Az0 = sqhl * Draw<float>::normal(pg, t * D), Az1 = 0.0f, A0 = 0.0f, A1 = 0.0f;
+                if constexpr (D == 2) Az1 = sqhl * Draw<float>::normal(pg, t * D + 1);
+                const float Xpre = xcol[t * BD];
                 float4 *hdr = rec;
                 rec += T;
-                // one chunk of four slots, slots below jlo are fixed forwards (a = 0)
+                // one chunk of four slots; slots below jlo are fixed forwards (a = 0).  All loads
+                // come before the stores, so the four exponentials overlap.
                 auto fwd_chunk = [&](int c, int jlo) {
-                    float av[4];
+                    float *px = xcol + c * (4 * BD);
+                    const float4 *pc = cfw + 4 * c;
+                    float X[4], a[4];
+                    float4 cn[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        const int n = 4 * c + j;
-                        av[j] = 0.0f;
+                        X[j] = px[j * BD];
+                        cn[j] = pc[j];
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) a[j] = j >= jlo ? rcp_approx(1.0f + ex2_approx(-X[j])) : 0.0f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
                         if (j >= jlo) {
-                            const float4 cn = cst[n];
-                            const float X = xs[n * bd];
-                            const float a = rcp_approx(1.0f + ex2_approx(-X));
-                            av[j] = a;
-                            A[0] = fmaf(cn.x, a, A[0]);
-                            float inc = fmaf(cn.x, fmaf(A[0], hl, Az[0]), ccs[n]);
+                            A0 = fmaf(cn[j].x, a[j], A0);
+                            float inc = fmaf(cn[j].x, fmaf(A0, hl, Az0), cn[j].z);
                             if constexpr (D == 2) {
-                                A[1] = fmaf(cn.y, a, A[1]);
-                                inc = fmaf(cn.y, fmaf(A[1], hl, Az[1]), inc);
+                                A1 = fmaf(cn[j].y, a[j], A1);
+                                inc = fmaf(cn[j].y, fmaf(A1, hl, Az1), inc);
                             }
-                            xs[n * bd] = X + inc;
+                            px[j * BD] = X[j] + inc;
                         }
                     }
-                    *rec = make_float4(av[0], av[1], av[2], av[3]);
+                    __stcs(rec, make_float4(a[0], a[1], a[2], a[3]));
                     rec += T;
                 };
                 fwd_chunk(t >> 2, t & 3);
                 for (int c = (t >> 2) + 1; c < nch; ++c) fwd_chunk(c, 0);
-                *hdr = make_float4(Xpre, A[0], D == 2 ? A[1] : 0.0f, 0.0f);
-                const float e = ex2_approx(xs[t * bd]);
+                __stcs(hdr, make_float4(Xpre, A0, A1, 0.0f));
+                const float e = ex2_approx(xcol[t * BD]);
                 disc *= rcp_approx(1.0f + e);
                 const float L = e * inv_dl;
                 float pn = 0.0f;
@@ -149,28 +167,31 @@ __global__ void __launch_bounds__(256, RQMC_ADJ_MIN_BLOCKS) lmm_adjoint_kernel(c
                 }
                 value += pn;
             }
-            // ---------------- reverse sweep (xs now holds the adjoints Xb); skipped for zero weights
-            for (int n = 0; n < 4 * nch; ++n) xs[n * bd] = 0.0f;
+            // ---------------- reverse sweep (xcol now holds the adjoints Xb); skipped for zero weights
+            for (int n = 0; n < 4 * nch; ++n) xcol[n * BD] = 0.0f;
             float Dcur = disc, G = 0.0f;
             for (int t = md.reverse ? nf - 1 : -1; t >= 0; --t) {
                 const int c0 = t >> 2;
                 rec -= (size_t)(1 + nch - c0) * T;
-                const float4 h4 = rec[0];
-                const float4 *__restrict__ ch = rec + T;      // chunk c at ch[(c - c0) T]
-                // software pipeline: the next chunk's a_n and vega are loaded one chunk ahead
-                float4 a4n = ch[(size_t)(nch - 1 - c0) * T];
-                float4 v4n = vega4[(size_t)(nch - 1) * T];
-                float Ar[D], Zs[D];
-                Ar[0] = h4.y;
-                if constexpr (D == 2) Ar[1] = h4.z;
-#pragma unroll
-                for (int f = 0; f < D; ++f) Zs[f] = Draw<float>::normal(pg, t * D + f);
+                const float4 h4 = __ldcs(rec);
+                const float4 ac = __ldcs(rec + T);              // chunk c0
+                // software pipeline over the chunks nch-1 .. c0, loaded two ahead
+                const float4 *q = rec + (size_t)(nch - c0) * T;  // chunk nch-1
+                float4 p0 = __ldcs(q);
+                q -= T;
+                float4 p1 = p0;
+                if (nch - 2 >= c0) {
+                    p1 = __ldcs(q);
+                    q -= T;
+                }
+                const float Z0 = Draw<float>::normal(pg, t * D);
+                const float Z1 = D == 2 ? Draw<float>::normal(pg, t * D + 1) : 0.0f;
                 // post-step value of the fixed forward, with the forward sweep's operations
-                const float4 ct = cst[t];
-                const float4 ac = ch[0];
-                const float a0 = (t & 3) == 0 ? ac.x : (t & 3) == 1 ? ac.y : (t & 3) == 2 ? ac.z : ac.w;
-                float inc = fmaf(ct.x, fmaf(fmaf(ct.x, a0, 0.0f), hl, sqhl * Zs[0]), ccs[t]);
-                if constexpr (D == 2) inc = fmaf(ct.y, fmaf(fmaf(ct.y, a0, 0.0f), hl, sqhl * Zs[1]), inc);
+                const float4 ct = cfw[t];
+                const int jt = t & 3;
+                const float a0 = jt == 0 ? ac.x : jt == 1 ? ac.y : jt == 2 ? ac.z : ac.w;
+                float inc = fmaf(ct.x, fmaf(fmaf(ct.x, a0, 0.0f), hl, sqhl * Z0), ct.z);
+                if constexpr (D == 2) inc = fmaf(ct.y, fmaf(fmaf(ct.y, a0, 0.0f), hl, sqhl * Z1), inc);
                 const float Y = h4.x + inc;
                 const float e = ex2_approx(Y);
                 const float aY = e * rcp_approx(1.0f + e);
@@ -185,55 +206,69 @@ __global__ void __launch_bounds__(256, RQMC_ADJ_MIN_BLOCKS) lmm_adjoint_kernel(c
                 }
                 G = fmaf(pn * dl, Dcur, G);
                 // an inactive lane (past N) follows a dummy path with zero adjoint source
-                xs[t * bd] += active ? ln2 * (dpn * dl * Dcur * L - aY * G) : 0.0f;
+                xcol[t * BD] += active ? ln2 * (dpn * dl * Dcur * L - aY * G) : 0.0f;
                 Dcur *= 1.0f + e;                             // D_{n-1} = D_n (1 + delta L_n)
-                float B[D];
-#pragma unroll
-                for (int f = 0; f < D; ++f) B[f] = 0.0f;
-                auto rev_chunk = [&](int c, int jlo, const float4 a4, const float4 v4) {
+                // top-down over the alive slots n: E = h A_n + sqrt(h) Z (A_n the step's prefix
+                // sum through n) and hB = h B_n = h sum_{m>=n} Xb_m sigma_m, per factor; the
+                // update of Xb_n is h (sigma.B) a (1 - a) = (h sigma . hB) a (1 - a) / h
+                float E0 = fmaf(h, h4.y, md.sqh * Z0), E1 = fmaf(h, h4.z, md.sqh * Z1);
+                float hB0 = 0.0f, hB1 = 0.0f;
+                float4 *vg = vega4 + (size_t)(nch - 1) * T;
+                auto rev_chunk = [&](int c, int jlo, const float4 a4) {
+                    float *px = xcol + c * (4 * BD);
+                    const float4 *pc = crv + 4 * c;
                     const float aa[4] = {a4.x, a4.y, a4.z, a4.w};
-                    float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                    float Xb[4], vv[4];
+                    float4 cn[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        Xb[j] = px[j * BD];
+                        cn[j] = pc[j];
+                    }
 #pragma unroll
                     for (int j = 3; j >= 0; --j) {
-                        const int n = 4 * c + j;
+                        vv[j] = 0.0f;
                         if (j >= jlo) {
+                            // sigma_bar = Xb (h (A_n - sigma_n) + sqrt(h) Z) + h a_n B_n, per factor
                             const float a = aa[j];
-                            const float4 cn = cst[n];
-                            const float Xb = xs[n * bd];
-                            B[0] = fmaf(Xb, cn.x, B[0]);
-                            float sB = cn.x * B[0];
-                            float v = cn.z * l2e * fmaf(Xb, fmaf(md.h, Ar[0] - cn.x, md.sqh * Zs[0]), md.h * a * B[0]);
-                            Ar[0] = fmaf(-cn.x, a, Ar[0]);
+                            hB0 = fmaf(Xb[j], cn[j].x, hB0);
+                            float S = cn[j].x * hB0;              // h^2 sigma.B
+                            float v = cn[j].z * fmaf(Xb[j], E0 - cn[j].x, a * hB0);
+                            E0 = fmaf(-cn[j].x, a, E0);
                             if constexpr (D == 2) {
-                                B[1] = fmaf(Xb, cn.y, B[1]);
-                                sB = fmaf(cn.y, B[1], sB);
-                                v = fmaf(cn.w * l2e, fmaf(Xb, fmaf(md.h, Ar[1] - cn.y, md.sqh * Zs[1]), md.h * a * B[1]), v);
-                                Ar[1] = fmaf(-cn.y, a, Ar[1]);
+                                hB1 = fmaf(Xb[j], cn[j].y, hB1);
+                                S = fmaf(cn[j].y, hB1, S);
+                                v = fmaf(cn[j].w, fmaf(Xb[j], E1 - cn[j].y, a * hB1), v);
+                                E1 = fmaf(-cn[j].y, a, E1);
                             }
-                            vv[j] += v;
-                            xs[n * bd] = fmaf(md.h * sB, a * (1.0f - a), Xb);
+                            vv[j] = v;
+                            px[j * BD] = fmaf(S, inv_h * fmaf(-a, a, a), Xb[j]);   // + h (sigma.B) a (1 - a)
                         }
                     }
-                    vega4[(size_t)c * T] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    red_add_v4(vg, vv);
+                    vg -= T;
                 };
                 for (int c = nch - 1; c > c0; --c) {
-                    const float4 a4 = a4n, v4 = v4n;
-                    a4n = ch[(size_t)(c - 1 - c0) * T];
-                    v4n = vega4[(size_t)(c - 1) * T];
-                    rev_chunk(c, 0, a4, v4);
+                    const float4 a4 = p0;
+                    p0 = p1;
+                    if (c - 2 >= c0) {
+                        p1 = __ldcs(q);
+                        q -= T;
+                    }
+                    rev_chunk(c, 0, a4);
                 }
-                rev_chunk(c0, t & 3, a4n, v4n);
+                rev_chunk(c0, jt, p0);
             }
             if (active) {
                 atomicAdd(accs, value);
-                for (int n = 0; n < nf; ++n) atomicAdd(accs + (size_t)(1 + n) * T, xs[n * bd] * md.invL0ln2[n]);
+                for (int n = 0; n < nf; ++n) atomicAdd(accs + (size_t)(1 + n) * T, xcol[n * BD] * md.invL0ln2[n]);
             }
         }
         // ---------------- unit flush: sum the CTA's columns in double
         __syncthreads();
         const int nrow = 1 + 2 * nf + nf * nK;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        const uint32_t col0 = blockIdx.x * blockDim.x;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = BD >> 5;
+        const uint32_t col0 = blockIdx.x * BD;
         for (int rw = warp; rw < nrow; rw += nw) {
             // output row rw: value, delta_n, vega_n, prices; columns of this CTA's threads
             float *p;
@@ -246,7 +281,7 @@ __global__ void __launch_bounds__(256, RQMC_ADJ_MIN_BLOCKS) lmm_adjoint_kernel(c
                 cs = 4;
             } else { p = sc.acc + (size_t)(NF + 1 + NF + (rw - 1 - 2 * nf)) * T + col0; cs = 1; }
             double s = 0.0;
-            for (int c = lane; c < (int)blockDim.x; c += 32) {
+            for (int c = lane; c < BD; c += 32) {
                 s += (double)__ldcg(p + (size_t)c * cs);   // from L2: the columns were reduced there
                 p[(size_t)c * cs] = 0.0f;
             }
@@ -265,12 +300,12 @@ template <int NF, int D, int SEQ>
 static cudaError_t launch_adj_t(const Plan &pl, cudaStream_t st) {
     auto kern = lmm_adjoint_kernel<NF, D, SEQ>;
     size_t a, b, c;
-    const size_t smem = adj_smem_layout<NF>(pl.gen, pl.threads, &a, &b, &c);
+    const size_t smem = adj_smem_layout<NF>(pl.gen, &a, &b, &c);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<pl.grid, pl.threads, smem, st>>>(pl.gen, *pl.adjm, pl.adjs, pl.red);
+    kern<<<pl.grid, kAdjThreads, smem, st>>>(pl.gen, *pl.adjm, pl.adjs, pl.red);
     return cudaGetLastError();
 }
 
@@ -278,18 +313,17 @@ template <int NF, int D, int SEQ>
 static int grid_adj_t(const Plan &pl, int mode) {
     auto kern = lmm_adjoint_kernel<NF, D, SEQ>;
     size_t a, b, c;
-    const size_t smem = adj_smem_layout<NF>(pl.gen, pl.threads, &a, &b, &c);
+    const size_t smem = adj_smem_layout<NF>(pl.gen, &a, &b, &c);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, pl.threads, smem);
-    if (mode == 2) return occ;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kAdjThreads, smem);
     if (occ < 1) occ = 1;
     return (int)std::min<unsigned long long>(pl.red.units, (unsigned long long)occ * sms);
 }
 
-// mode 0: launch, mode 1: return the persistent grid size, mode 2: resident CTAs per SM
+// mode 0: launch, mode 1: return the persistent grid size
 template <int SEQ>
 int adjoint_seq(const Plan &pl, cudaStream_t st, int mode) {
     const bool two = pl.adjm->d == 2;

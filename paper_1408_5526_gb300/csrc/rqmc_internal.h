@@ -193,7 +193,7 @@ int64_t batch_output_size(const Plan &pl);
 void batch_destroy(Plan &pl);
 int batch_ppt(const Plan &pl);
 int adjoint_grid(const Plan &pl);
-int adjoint_occupancy(const Plan &pl);   // resident CTAs per SM at pl.threads
+constexpr int kAdjointThreads = 256;   // CTA size of the adjoint kernel
 int occupancy_blocks(const Plan &pl);
 
 // ---- errors
