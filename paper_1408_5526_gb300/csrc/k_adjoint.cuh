@@ -12,7 +12,8 @@
 // The forward sweep stores, per step, a header (the pre-step X of the forward fixed at that
 // step, the step's prefix total A) and the a_n in 16-byte chunks aligned to absolute forward
 // slots, interleaved by thread in global scratch: one coalesced 128-bit streaming store per
-// four forwards, read back once by the reverse sweep two chunks ahead.  The vega accumulators
+// four forwards, read back once by the reverse sweep (prefetched into L2 one step ahead, then
+// into registers two chunks ahead).  The vega accumulators
 // use the same chunking and are updated by vector reductions that the thread does not wait
 // for.  With Xb_n = dV/dX_n and B_n = sum_{m>=n} Xb_m sigma_m, the reverse sweep of a step
 // visits the alive slots top-down and applies
@@ -46,6 +47,11 @@ constexpr int kAdjThreads = kAdjointThreads;
 // Shared memory: [generator stage][forward constants (sigma_1, sigma_2, cc, 0) x NF]
 //                [reverse constants (h sigma_1, h sigma_2, b_1 log2 e, b_2 log2 e) x NF]
 //                [per-thread state x NF x kAdjThreads]  (forward X, then the adjoints Xb)
+// L2 prefetch: no register is written, so the thread does not wait for it.
+__device__ __forceinline__ void prefetch_l2(const void *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int NF>
 __host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, size_t *o_fw, size_t *o_rv,
                                                            size_t *o_st) {
@@ -173,6 +179,11 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
             for (int t = md.reverse ? nf - 1 : -1; t >= 0; --t) {
                 const int c0 = t >> 2;
                 rec -= (size_t)(1 + nch - c0) * T;
+                if (t > 0) {   // the previous step's records into L2, a whole step ahead
+                    const int c0p = (t - 1) >> 2;
+                    const float4 *pv = rec - (size_t)(1 + nch - c0p) * T;
+                    for (int k = 0; k <= nch - c0p; ++k) prefetch_l2(pv + (size_t)k * T);
+                }
                 const float4 h4 = __ldcs(rec);
                 const float4 ac = __ldcs(rec + T);              // chunk c0
                 // software pipeline over the chunks nch-1 .. c0, loaded two ahead
