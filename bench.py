@@ -33,6 +33,10 @@ import numpy as np  # noqa: E402
 N_FWD, N_PATHS, M_REPL, SEED = 40, 65536, 64, 1
 SEQS = ("rasrap", "sobol_ds", "philox")
 L2_FLUSH_BYTES = 512 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one lmm_caplet_kernel<40, 1, float> launch
+# (Rasrap) of this workload, from an ncu capture of the kernel as committed; set to None
+# whenever that kernel changes until it is captured again.
+LMM_TRAFFIC_BYTES = 723.2e3
 
 
 def _peaks():
@@ -196,7 +200,8 @@ def run_ours(args, rank, world):
     roof = {"bound": "alu", "pipe": "sfu" if a_mufu / mufu_peak >= a_fma / fma_peak else "fma",
             "achieved": round(a_mufu / 1e12, 4), "peak": round(mufu_peak / 1e12, 4),
             "unit": "T SFU issue slots/s (ex2 = 1/2 slot, rcp/lg2 = 1 slot)",
-            "frac": round(a_mufu / mufu_peak, 4), "traffic": None,
+            "frac": round(a_mufu / mufu_peak, 4), "traffic": LMM_TRAFFIC_BYTES,
+            "traffic_unit": "DRAM bytes per launch (ncu, Rasrap launch; tables only)",
             "fma_achieved": round(a_fma / 1e12, 3), "fma_peak": round(fma_peak / 1e12, 3),
             "fma_frac": round(a_fma / fma_peak, 4),
             "kernel": "lmm_caplet_kernel<40,float> + theta_kernel",
