@@ -11,8 +11,9 @@ checked against the FP64 oracle (two replications at full N) before timing.
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the oracle is the reference implementation).
-Under torchrun each rank prices its own replications (seed + rank): weak
-scaling with no data-path collective.
+Under torchrun each rank prices its own contiguous range of N points of every
+replication (plan offset = rank x N, weak scaling); each step ends with the one
+exchange of the estimator, an all-reduce of the M x 120 theta values per sequence.
 """
 from __future__ import annotations
 
@@ -115,15 +116,16 @@ class ClockSampler:
 
 def run_ours(args, rank, world):
     import torch
-    from paper_1408_5526_gb300 import inputs, rqmc
+    from paper_1408_5526_gb300 import inputs, rqmc, shard
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     rqmc.load()
     lm = inputs.lmm_flat(N_FWD)
     K = inputs.LMM_STRIKES
-    seed = SEED + rank
-    plans = [rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, s, seed, prec="fp32") for s in SEQS]
+    seed = SEED
+    offset, n_local = shard.point_range(rank, world, N_PATHS * world)
+    plans = [rqmc.Plan.caplets(lm, K, n_local, M_REPL, s, seed, prec="fp32", offset=offset) for s in SEQS]
     outs = [torch.empty(p.output_size(), dtype=torch.float64, device=dev) for p in plans]
     stream = torch.cuda.current_stream()
 
@@ -147,6 +149,8 @@ def run_ours(args, rank, world):
     def step():
         for p, o in zip(plans, outs):
             p.execute(o, stream)
+            if world > 1:
+                shard.combine_theta(o, n_local)
 
     for _ in range(args.warmup):
         step()
@@ -165,6 +169,8 @@ def run_ours(args, rank, world):
                 kev[k][j][0].record(stream)
                 p.execute(o, stream)
                 kev[k][j][1].record(stream)
+                if world > 1:
+                    shard.combine_theta(o, n_local)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         time.sleep(0.25)
@@ -221,7 +227,8 @@ def run_ours(args, rank, world):
                        "N": N_PATHS, "M": M_REPL, "strikes": list(map(float, K)), "sequences": list(SEQS),
                        "precision": "fp32 paths, Kahan sums, fp64 replication reduction",
                        "path_steps_per_step": N_PATHS * M_REPL * N_FWD * len(SEQS) * world,
-                       "parallelism": f"replicas x{world} (seed + rank)",
+                       "parallelism": (f"point ranges x{world}: offset = rank x N, "
+                                       "theta all-reduced per sequence per step") if world > 1 else "1 GPU",
                        "l2": "flushed (512 MiB write) before every timed step, outside its interval",
                        "timing": "sum of per-step CUDA-event intervals"},
             "parity": parity,
