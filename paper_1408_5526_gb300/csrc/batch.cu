@@ -1,12 +1,13 @@
 // batch.cu -- host side of the batched launch: instrument validation, per-instrument
-// randomization tables and models, longest-first work list, CUDA-graph capture of
-// [ticket reset -> persistent kernel -> per-instrument theta], and the tile autotuner.
+// randomization tables and models, longest-first work lists (one per work class: LMM
+// strips, MBS), CUDA-graph capture of [ticket reset -> the two persistent kernels as
+// parallel branches -> per-instrument theta], and the tile autotuner.
 //
 // The autotuner times the captured launch for several tile sizes (paths per thread) on a
 // copy of the batch with N capped at 8192 per instrument and keeps the fastest; the choice
 // is cached in a small JSON file keyed by GPU name, sequence and a hash of the batch
 // (path: $RQMC_AUTOTUNE_CACHE, default ~/.cache/rqmc_gb300/autotune.json;
-// RQMC_AUTOTUNE=0 skips tuning and uses 2 paths per thread).
+// RQMC_AUTOTUNE=0 skips tuning and uses 4 paths per thread).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -21,7 +22,7 @@
 #include <sys/stat.h>
 #include <vector>
 
-#include "k_lmm.cuh"
+#include "k_batch.cuh"
 
 namespace rqmc {
 
@@ -35,7 +36,9 @@ struct BatchPlan {
     size_t theta_doubles = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap = nullptr;
+    cudaStream_t cap = nullptr;                             // capture stream (class 0)
+    cudaStream_t side[kBatchClasses - 1] = {};              // classes 1.. (forked)
+    cudaEvent_t fork = nullptr, join[kBatchClasses - 1] = {};
     std::vector<BatchInst> insts;   // host copy (device pointers filled)
     size_t smem_lmm_base = 0;
 };
@@ -69,10 +72,10 @@ static size_t item_smem(const BatchInst &bi, int threads) {
     if (bi.kind == 0) {
         size_t a, b, c, d, e;
         switch (bi.bucket) {
-            case 16: return lmm_smem_layout<16, float>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
-            case 40: return lmm_smem_layout<40, float>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
-            case 80: return lmm_smem_layout<80, float>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
-            default: return lmm_smem_layout<160, float>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
+            case 16: return lmm_smem_layout<16, float, batch_ilp<16>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
+            case 40: return lmm_smem_layout<40, float, batch_ilp<40>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
+            case 80: return lmm_smem_layout<80, float, batch_ilp<80>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
+            default: return lmm_smem_layout<160, float, batch_ilp<160>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
         }
     }
     return stage_bytes(bi.g) + sizeof(float) * (2 * (size_t)nw + (size_t)bi.g.s + 1);
@@ -83,12 +86,14 @@ static double item_cost(const rqmc_instrument &d) {
     return d.kind == 0 ? 0.5 * d.size * (d.size + 1.0) : 3.0 * d.size;
 }
 
+// Items of each work class (see BatchLaunch), each list longest first.
 static rqmc_status build_work(BatchPlan &bp, int threads, int ppt, bool cap_n, std::vector<BatchInst> &insts,
-                              std::vector<BatchItem> &items, size_t &part_doubles, size_t &theta_doubles,
-                              size_t &smem) {
+                              std::vector<BatchItem> (&items)[kBatchClasses], size_t &part_doubles,
+                              size_t &theta_doubles, size_t (&smem)[kBatchClasses]) {
     const uint32_t tile = (uint32_t)(threads * ppt);
-    part_doubles = theta_doubles = smem = 0;
-    std::vector<std::pair<double, BatchItem>> order;
+    part_doubles = theta_doubles = 0;
+    for (auto &x : smem) x = 0;
+    std::vector<std::pair<double, BatchItem>> order[kBatchClasses];
     for (int i = 0; i < bp.n; ++i) {
         BatchInst &bi = insts[i];
         const uint64_t N = cap_n ? std::min<uint64_t>((uint64_t)bp.desc[i].N, 8192) : (uint64_t)bp.desc[i].N;
@@ -98,20 +103,23 @@ static rqmc_status build_work(BatchPlan &bp, int threads, int ppt, bool cap_n, s
         bi.theta_off = theta_doubles;
         part_doubles += (size_t)bp.M * bi.tiles_per_m * bi.nout;
         theta_doubles += (size_t)bp.M * bi.nout;
-        smem = std::max(smem, item_smem(bi, threads));
+        const int cls = batch_class(bi);
+        smem[cls] = std::max(smem[cls], item_smem(bi, threads));
         const double c = item_cost(bp.desc[i]);
         for (int m = 0; m < bp.M; ++m)
             for (uint32_t t = 0; t < bi.tiles_per_m; ++t) {
                 const uint32_t paths = std::min<uint64_t>(tile, N - (uint64_t)t * tile);
-                order.push_back({c * paths, BatchItem{(uint32_t)i, (uint32_t)m, t, 0u}});
+                order[cls].push_back({c * paths, BatchItem{(uint32_t)i, (uint32_t)m, t, 0u}});
             }
     }
-    std::stable_sort(order.begin(), order.end(),
-                     [](const std::pair<double, BatchItem> &a, const std::pair<double, BatchItem> &b) {
-                         return a.first > b.first;
-                     });
-    items.resize(order.size());
-    for (size_t k = 0; k < order.size(); ++k) items[k] = order[k].second;
+    for (int cls = 0; cls < kBatchClasses; ++cls) {
+        std::stable_sort(order[cls].begin(), order[cls].end(),
+                         [](const std::pair<double, BatchItem> &a, const std::pair<double, BatchItem> &b) {
+                             return a.first > b.first;
+                         });
+        items[cls].resize(order[cls].size());
+        for (size_t k = 0; k < order[cls].size(); ++k) items[cls][k] = order[cls][k].second;
+    }
     return RQMC_OK;
 }
 
@@ -128,35 +136,50 @@ static void free_work(BatchPlan &bp) {
 static rqmc_status setup_launch(BatchPlan &bp, int threads, int ppt, bool cap_n) {
     free_work(bp);
     std::vector<BatchInst> insts = bp.insts;
-    std::vector<BatchItem> items;
-    size_t part = 0, theta = 0, smem = 0;
+    std::vector<BatchItem> items[kBatchClasses];
+    size_t part = 0, theta = 0, smem[kBatchClasses] = {};
     build_work(bp, threads, ppt, cap_n, insts, items, part, theta, smem);
-    if (smem > 227 * 1024) { set_error("batch: an instrument needs more shared memory than a CTA has"); return RQMC_EUNSUPPORTED; }
+    if (*std::max_element(smem, smem + kBatchClasses) > 227 * 1024) {
+        set_error("batch: an instrument needs more shared memory than a CTA has");
+        return RQMC_EUNSUPPORTED;
+    }
     Carve cv;
     const size_t o_inst = cv.take(sizeof(BatchInst) * insts.size());
-    const size_t o_items = cv.take(sizeof(BatchItem) * items.size());
+    size_t o_items[kBatchClasses];
+    for (int k = 0; k < kBatchClasses; ++k) o_items[k] = cv.take(sizeof(BatchItem) * std::max<size_t>(items[k].size(), 1));
     const size_t o_cnt = cv.take(sizeof(uint32_t) * 4);
     const size_t o_part = cv.take(sizeof(double) * part);
     const size_t o_theta = cv.take(sizeof(double) * theta);
     cudaError_t e = cudaMalloc(&bp.d_work, cv.off);
     if (e != cudaSuccess) { bp.d_work = nullptr; set_error("batch: work allocation failed"); return RQMC_ENOMEM; }
     unsigned char *d = static_cast<unsigned char *>(bp.d_work);
-    if (cudaMemcpy(d + o_inst, insts.data(), sizeof(BatchInst) * insts.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d + o_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    bool up = cudaMemcpy(d + o_inst, insts.data(), sizeof(BatchInst) * insts.size(), cudaMemcpyHostToDevice) ==
+              cudaSuccess;
+    for (int k = 0; k < kBatchClasses; ++k)
+        up = up && (items[k].empty() || cudaMemcpy(d + o_items[k], items[k].data(), sizeof(BatchItem) * items[k].size(),
+                                                   cudaMemcpyHostToDevice) == cudaSuccess);
+    if (!up) {
         set_error("batch: upload failed");
         return RQMC_ECUDA;
     }
     BatchLaunch &bl = bp.bl;
     bl.insts = reinterpret_cast<const BatchInst *>(d + o_inst);
-    bl.items = reinterpret_cast<const BatchItem *>(d + o_items);
-    bl.n_items = (uint32_t)items.size();
+    for (int k = 0; k < kBatchClasses; ++k) {
+        bl.items[k] = reinterpret_cast<const BatchItem *>(d + o_items[k]);
+        bl.n_items[k] = (uint32_t)items[k].size();
+        bl.smem[k] = smem[k];
+    }
     bl.n_inst = (uint32_t)insts.size();
     bl.counter = reinterpret_cast<uint32_t *>(d + o_cnt);
     bl.partials = reinterpret_cast<double *>(d + o_part);
     bl.theta = reinterpret_cast<double *>(d + o_theta);
     bl.threads = threads;
     bl.ppt = ppt;
-    bl.smem = smem;
+    bl.fork = bp.fork;
+    for (int k = 0; k + 1 < kBatchClasses; ++k) {
+        bl.side[k] = bp.side[k];
+        bl.join[k] = bp.join[k];
+    }
     bp.theta_doubles = theta;
     // one direct launch sets kernel attributes outside the capture, then capture the graph
     if ((e = launch_batch(bl, bp.seq, bp.cap)) != cudaSuccess) return RQMC_ECUDA;
@@ -247,16 +270,16 @@ static float time_launch(BatchPlan &bp) {
 
 static int autotune(BatchPlan &bp) {
     const char *env = std::getenv("RQMC_AUTOTUNE");
-    if (env && std::strcmp(env, "0") == 0) return 2;
+    if (env && std::strcmp(env, "0") == 0) return 4;
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
     const std::string key = batch_key(bp);
     auto kv = cache_read();
     auto it = kv.find(key);
     if (it != kv.end() && it->second >= 1 && it->second <= 16) return it->second;
-    int best = 2;
+    int best = 4;
     float best_ms = 1e30f;
-    for (int ppt : {1, 2, 4, 8}) {
+    for (int ppt : {4, 8, 16}) {   // multiples of every bucket's paths per thread in lockstep
         if (setup_launch(bp, 256, ppt, true) != RQMC_OK) continue;
         const float ms = time_launch(bp);
         if (ms < best_ms) { best_ms = ms; best = ppt; }
@@ -314,13 +337,18 @@ extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *inst, int n, int M
         rqmc_plan_destroy(pl);
         return st;
     };
-    if (cudaStreamCreateWithFlags(&bp->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(RQMC_ECUDA);
+    bool made = cudaStreamCreateWithFlags(&bp->cap, cudaStreamNonBlocking) == cudaSuccess &&
+                cudaEventCreateWithFlags(&bp->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k + 1 < kBatchClasses; ++k)
+        made = made && cudaStreamCreateWithFlags(&bp->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&bp->join[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!made) return fail(RQMC_ECUDA);
     // generator tables of every instrument (instrument index i in the counters), models
     std::vector<Plan> sub(n);
     std::vector<GenLayout> gls(n);
     Carve cv;
     std::vector<size_t> base(n), model_off(n);
-    int n_lmm = 0, n_mbs = 0;
+    int n_class[kBatchClasses] = {};
     for (int i = 0; i < n; ++i) {
         Plan &s = sub[i];
         s.kind = inst[i].kind == 0 ? kCaplets : kMbs;
@@ -338,10 +366,10 @@ extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *inst, int n, int M
         base[i] = cv.take(ci.off);
         if (inst[i].kind == 0) {
             model_off[i] = cv.take(sizeof(LmmModel<float>));
-            ++n_lmm;
+            ++n_class[lmm_bucket_of(inst[i].size) == 160 ? 0 : 2];
         } else {
             model_off[i] = cv.take(sizeof(MbsModel<float>) + sizeof(float) * (inst[i].size + 1));
-            ++n_mbs;
+            ++n_class[1];
         }
     }
     const size_t status_off = cv.take(sizeof(uint32_t) * 4);
@@ -394,7 +422,8 @@ extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *inst, int n, int M
     pl->threads = 256;
     pl->ppt = ppt;
     pl->nout = 0;
-    pl->launches = 3;
+    pl->launches = 1;   // theta
+    for (int k = 0; k < kBatchClasses; ++k) pl->launches += n_class[k] > 0 ? 1 : 0;
     *plan = pl;
     return RQMC_OK;
 }
@@ -419,9 +448,16 @@ void batch_destroy(Plan &pl) {
     if (!pl.batch) return;
     BatchPlan &bp = *pl.batch;
     if (bp.cap) cudaStreamSynchronize(bp.cap);
+    for (auto s : bp.side)
+        if (s) cudaStreamSynchronize(s);
     free_work(bp);
     if (bp.d_tables) cudaFree(bp.d_tables);
     if (bp.cap) cudaStreamDestroy(bp.cap);
+    for (auto s : bp.side)
+        if (s) cudaStreamDestroy(s);
+    if (bp.fork) cudaEventDestroy(bp.fork);
+    for (auto ev : bp.join)
+        if (ev) cudaEventDestroy(ev);
     delete pl.batch;
     pl.batch = nullptr;
 }

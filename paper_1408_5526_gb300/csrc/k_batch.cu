@@ -5,7 +5,7 @@
 namespace rqmc {
 
 template <int SEQ>
-cudaError_t launch_batch_seq(const BatchLaunch &bl, cudaStream_t st);
+cudaError_t launch_batch_seq(const BatchLaunch &bl, int kind, cudaStream_t st);
 
 // theta of every instrument: block = instrument, threads over (m, o), tiles summed in order
 __global__ void batch_theta_kernel(const BatchInst *__restrict__ insts, const double *__restrict__ partials,
@@ -22,13 +22,32 @@ __global__ void batch_theta_kernel(const BatchInst *__restrict__ insts, const do
     }
 }
 
+// [reset the tickets] -> fork: classes 1.. on side streams | class 0 on st -> join ->
+// theta.  No kernel waits on another, so any co-scheduling of them is safe.
 cudaError_t launch_batch(const BatchLaunch &bl, int seq, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(bl.counter, 0, sizeof(uint32_t), st);
+    cudaError_t e = cudaMemsetAsync(bl.counter, 0, kBatchClasses * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
-#define RQMC_L(S) launch_batch_seq<S>(bl, st)
-    e = RQMC_SEQ_DISPATCH(seq, RQMC_L);
+    bool forked[kBatchClasses] = {};
+    if ((e = cudaEventRecord(bl.fork, st)) != cudaSuccess) return e;
+    for (int k = 1; k < kBatchClasses; ++k) {
+        if (bl.n_items[k] == 0) continue;
+        cudaStream_t sk = bl.side[k - 1];
+        if ((e = cudaStreamWaitEvent(sk, bl.fork, 0)) != cudaSuccess) return e;
+#define RQMC_L(S) launch_batch_seq<S>(bl, k, sk)
+        e = RQMC_SEQ_DISPATCH(seq, RQMC_L);
 #undef RQMC_L
-    if (e != cudaSuccess) return e;
+        if (e != cudaSuccess) return e;
+        if ((e = cudaEventRecord(bl.join[k - 1], sk)) != cudaSuccess) return e;
+        forked[k] = true;
+    }
+    if (bl.n_items[0] > 0) {
+#define RQMC_L(S) launch_batch_seq<S>(bl, 0, st)
+        e = RQMC_SEQ_DISPATCH(seq, RQMC_L);
+#undef RQMC_L
+        if (e != cudaSuccess) return e;
+    }
+    for (int k = 1; k < kBatchClasses; ++k)
+        if (forked[k] && (e = cudaStreamWaitEvent(st, bl.join[k - 1], 0)) != cudaSuccess) return e;
     batch_theta_kernel<<<bl.n_inst, 256, 0, st>>>(bl.insts, bl.partials, bl.theta);
     return cudaGetLastError();
 }

@@ -14,6 +14,21 @@
 
 namespace rqmc {
 
+// Paths per thread in lockstep per bucket, sized to the register budget of the bucket's
+// work class (16/40/80 forwards: 2 CTAs per SM, 128 registers; 160: 1 CTA per SM).  MBS
+// paths stay one per thread: their month is dominated by the branches of the inverse CDF
+// and the arctangent, which keep the compiler from interleaving paths, so lockstep copies
+// only add code (4 and 8 paths measured 18 % slower than 1 on the 128 MBS of the
+// 512-instrument batch).
+template <int NF>
+__host__ __device__ constexpr int batch_ilp() {
+    return NF <= 16 ? 4 : NF <= 40 ? 2 : 1;
+}
+constexpr int kBatchMbsIlp = 1;
+
+// Work class of an instrument (see BatchLaunch).
+__host__ __device__ inline int batch_class(const BatchInst &bi) { return bi.kind != 0 ? 1 : bi.bucket == 160 ? 0 : 2; }
+
 template <int NF, int SEQ>
 __device__ __forceinline__ void batch_lmm(const BatchInst &bi, const BatchItem &it, const GenView &gv,
                                           const RedParams &r, unsigned char *smem_raw) {
@@ -22,8 +37,9 @@ __device__ __forceinline__ void batch_lmm(const BatchInst &bi, const BatchItem &
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const LmmModel<float> *md = bi.lmm;
     const int nK = md->nK, nout = r.nout;
+    constexpr int P = batch_ilp<NF>();
     size_t o_cst, o_x0, o_z, o_buf, o_acc;
-    lmm_smem_layout<NF, float>(bi.g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
+    lmm_smem_layout<NF, float, P>(bi.g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
     float *zb = reinterpret_cast<float *>(smem_raw + o_z) + threadIdx.x;
     V2 *cst = reinterpret_cast<V2 *>(smem_raw + o_cst);
     float *X0 = reinterpret_cast<float *>(smem_raw + o_x0);
@@ -39,14 +55,19 @@ __device__ __forceinline__ void batch_lmm(const BatchInst &bi, const BatchItem &
     zero_acc(acc, cmp, nw * nout);
     const LmmScal<float> sc{md->nf, md->nK, md->dl, md->inv_dl, md->disc0, md->hc, md->sqhc};
     __syncthreads();
-    for (int pp = 0; pp < r.ppt; ++pp) {
-        const uint32_t i = it.tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
-        const bool active = i < r.N;
-        if (!__any_sync(0xffffffffu, active)) break;
-        PathGen<SEQ> pg[1];
-        pg[0].init(gv, active ? i : 0u);
-        const bool act[1] = {active};
-        lmm_path<NF, SEQ, float, 1>(pg, act, sc, cst, X0, Ks, zb, wbuf, acc + warp * nout, cmp + warp * nout, lane);
+    for (int pp = 0; pp < r.ppt; pp += P) {
+        PathGen<SEQ> pg[P];
+        bool act[P];
+        bool any = false;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const uint32_t i = it.tile * r.tile + (uint32_t)((pp + p) * blockDim.x + threadIdx.x);
+            act[p] = pp + p < r.ppt && i < r.N;
+            any = any || act[p];
+            pg[p].init(gv, act[p] ? i : 0u);
+        }
+        if (!__any_sync(0xffffffffu, any)) break;
+        lmm_path<NF, SEQ, float, P>(pg, act, sc, cst, X0, Ks, zb, wbuf, acc + warp * nout, cmp + warp * nout, lane);
     }
     flush_unit(r, it.m * bi.tiles_per_m + it.tile, acc, cmp);
 }
@@ -62,22 +83,33 @@ __device__ __forceinline__ void batch_mbs(const BatchInst &bi, const BatchItem &
     for (int k = threadIdx.x; k <= md.months; k += blockDim.x) ck[k] = md.ck[k];
     zero_acc(acc, cmp, nw);
     __syncthreads();
-    for (int pp = 0; pp < r.ppt; ++pp) {
-        const uint32_t i = it.tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
-        const bool active = i < r.N;
-        if (!__any_sync(0xffffffffu, active)) break;
-        PathGen<SEQ> pg;
-        pg.init(gv, active ? i : 0u);
-        const float v = mbs_path<float, SEQ>(pg, md, ck);
-        warp_accumulate<float>(active ? v : 0.0f, acc + warp, cmp + warp, 0, lane);
+    constexpr int P = kBatchMbsIlp;
+    for (int pp = 0; pp < r.ppt; pp += P) {
+        PathGen<SEQ> pg[P];
+        bool act[P];
+        bool any = false;
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const uint32_t i = it.tile * r.tile + (uint32_t)((pp + p) * blockDim.x + threadIdx.x);
+            act[p] = pp + p < r.ppt && i < r.N;
+            any = any || act[p];
+            pg[p].init(gv, act[p] ? i : 0u);
+        }
+        if (!__any_sync(0xffffffffu, any)) break;
+        float v[P];
+        mbs_paths<float, SEQ, P>(pg, md, ck, v);
+#pragma unroll
+        for (int p = 0; p < P; ++p) warp_accumulate<float>(act[p] ? v[p] : 0.0f, acc + warp, cmp + warp, 0, lane);
     }
     flush_unit(r, it.m * bi.tiles_per_m + it.tile, acc, cmp);
 }
 
-template <int SEQ>
-__global__ void __launch_bounds__(256, 1) batch_kernel(const BatchInst *__restrict__ insts,
-                                                       const BatchItem *__restrict__ items, uint32_t n_items,
-                                                       uint32_t *counter, double *partials, int ppt) {
+// One persistent kernel per work class KIND (see BatchLaunch).
+template <int SEQ, int KIND>
+__global__ void __launch_bounds__(256, KIND == 0 ? 1 : KIND == 1 ? 4 : 2) batch_kernel(const BatchInst *__restrict__ insts,
+                                                                    const BatchItem *__restrict__ items,
+                                                                    uint32_t n_items, uint32_t *counter,
+                                                                    double *partials, int ppt) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_ticket;
     for (;;) {
@@ -99,12 +131,13 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(const BatchInst *__restri
         r.N = bi.N;
         r.partials = partials + bi.part_off;
         r.status = nullptr;
-        if (bi.kind == 0) {
+        if constexpr (KIND == 0) {
+            batch_lmm<160, SEQ>(bi, it, gv, r, smem_raw);
+        } else if constexpr (KIND == 2) {
             switch (bi.bucket) {
                 case 16: batch_lmm<16, SEQ>(bi, it, gv, r, smem_raw); break;
                 case 40: batch_lmm<40, SEQ>(bi, it, gv, r, smem_raw); break;
-                case 80: batch_lmm<80, SEQ>(bi, it, gv, r, smem_raw); break;
-                default: batch_lmm<160, SEQ>(bi, it, gv, r, smem_raw); break;
+                default: batch_lmm<80, SEQ>(bi, it, gv, r, smem_raw); break;
             }
         } else {
             batch_mbs<SEQ>(bi, it, gv, r, smem_raw);
@@ -112,21 +145,30 @@ __global__ void __launch_bounds__(256, 1) batch_kernel(const BatchInst *__restri
     }
 }
 
-template <int SEQ>
-cudaError_t launch_batch_seq(const BatchLaunch &bl, cudaStream_t st) {
-    auto kern = batch_kernel<SEQ>;
-    if (bl.smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bl.smem);
+template <int SEQ, int KIND>
+cudaError_t launch_batch_class(const BatchLaunch &bl, cudaStream_t st) {
+    auto kern = batch_kernel<SEQ, KIND>;
+    const size_t smem = bl.smem[KIND];
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     int occ = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bl.threads, bl.smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, bl.threads, smem);
     if (occ < 1) occ = 1;
-    const unsigned grid = (unsigned)std::min<unsigned long long>(bl.n_items, (unsigned long long)occ * sms);
-    kern<<<grid, bl.threads, bl.smem, st>>>(bl.insts, bl.items, bl.n_items, bl.counter, bl.partials, bl.ppt);
+    const unsigned grid = (unsigned)std::min<unsigned long long>(bl.n_items[KIND], (unsigned long long)occ * sms);
+    kern<<<grid, bl.threads, smem, st>>>(bl.insts, bl.items[KIND], bl.n_items[KIND], bl.counter + KIND, bl.partials,
+                                         bl.ppt);
     return cudaGetLastError();
+}
+
+template <int SEQ>
+cudaError_t launch_batch_seq(const BatchLaunch &bl, int kind, cudaStream_t st) {
+    return kind == 0   ? launch_batch_class<SEQ, 0>(bl, st)
+           : kind == 1 ? launch_batch_class<SEQ, 1>(bl, st)
+                       : launch_batch_class<SEQ, 2>(bl, st);
 }
 
 }  // namespace rqmc

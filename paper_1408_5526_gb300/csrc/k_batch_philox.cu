@@ -2,5 +2,5 @@
 #include "k_batch.cuh"
 
 namespace rqmc {
-template cudaError_t launch_batch_seq<kPhilox>(const BatchLaunch &bl, cudaStream_t st);
+template cudaError_t launch_batch_seq<kPhilox>(const BatchLaunch &bl, int kind, cudaStream_t st);
 }  // namespace rqmc

@@ -35,10 +35,11 @@ __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsMo
             const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
             const bool active = i < r.N;
             if (!__any_sync(0xffffffffu, active)) break;
-            PathGen<SEQ> pg;
-            pg.init(gv, active ? i : 0u);
-            const T v = mbs_path<T, SEQ>(pg, md, ck);
-            warp_accumulate<T>(active ? v : T(0), acc + warp, cmp + warp, 0, lane);
+            PathGen<SEQ> pg[1];
+            pg[0].init(gv, active ? i : 0u);
+            T v[1];
+            mbs_paths<T, SEQ, 1>(pg, md, ck, v);
+            warp_accumulate<T>(active ? v[0] : T(0), acc + warp, cmp + warp, 0, lane);
         }
         flush_unit(r, u, acc, cmp);
     }

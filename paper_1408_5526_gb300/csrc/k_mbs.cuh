@@ -1,4 +1,4 @@
-// k_mbs.cuh -- one path of the mortgage-backed-security model (Sec. 6), shared by the MBS
+// k_mbs.cuh -- paths of the mortgage-backed-security model (Sec. 6), shared by the MBS
 // kernel and the batched kernel.
 #pragma once
 #include "paths_common.cuh"
@@ -15,21 +15,37 @@ __device__ __forceinline__ double mbs_exp<double>(double x) { return exp(x); }
 __device__ __forceinline__ float mbs_atan(float x) { return atanf(x); }
 __device__ __forceinline__ double mbs_atan(double x) { return atan(x); }
 
-template <typename T, int SEQ>
-__device__ __forceinline__ T mbs_path(PathGen<SEQ> &pg, const MbsModel<T> &md, const T *__restrict__ ck) {
-    T ip = md.i0, u = md.u1, rr = T(1), v = T(0), vc = T(0);
-    for (int k = 1; k <= md.months; ++k) {
-        const T z = Draw<T>::normal(pg, k - 1);
-        const T ik = ip * mbs_exp<T>(fmaT(md.sz, z, md.lk0));
-        const T w = fmaT(md.K2, mbs_atan(fmaT(md.K3, ik, md.K4)), md.K1);
-        const T mk = md.c * rr * ((T(1) - w) + w * ck[k]);
-        if constexpr (sizeof(T) == 4) kahan_add(v, vc, u * mk);
-        else v += u * mk;
-        u *= fast_rcp<T>(T(1) + ik);
-        rr *= T(1) - w;
-        ip = ik;
+// P paths in lockstep (same arithmetic per path as P = 1): they share the c_k loads and
+// the control flow and give the thread P independent dependency chains.
+template <typename T, int SEQ, int P>
+__device__ __forceinline__ void mbs_paths(PathGen<SEQ> (&pg)[P], const MbsModel<T> &md, const T *__restrict__ ck,
+                                          T (&out)[P]) {
+    T ip[P], u[P], rr[P], v[P], vc[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        ip[p] = md.i0;
+        u[p] = md.u1;
+        rr[p] = T(1);
+        v[p] = T(0);
+        vc[p] = T(0);
     }
-    return v - vc;
+    for (int k = 1; k <= md.months; ++k) {
+        const T c = ck[k];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            const T z = Draw<T>::normal(pg[p], k - 1);
+            const T ik = ip[p] * mbs_exp<T>(fmaT(md.sz, z, md.lk0));
+            const T w = fmaT(md.K2, mbs_atan(fmaT(md.K3, ik, md.K4)), md.K1);
+            const T mk = md.c * rr[p] * ((T(1) - w) + w * c);
+            if constexpr (sizeof(T) == 4) kahan_add(v[p], vc[p], u[p] * mk);
+            else v[p] += u[p] * mk;
+            u[p] *= fast_rcp<T>(T(1) + ik);
+            rr[p] *= T(1) - w;
+            ip[p] = ik;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) out[p] = v[p] - vc[p];
 }
 
 }  // namespace rqmc

@@ -111,14 +111,20 @@ struct BatchItem {
     uint32_t inst, m, tile, pad;
 };
 
+// Work classes, each with its own persistent kernel, register budget and ticket queue:
+// 0 = LMM strips of the 160-forward bucket (one 256-thread CTA per SM), 1 = MBS (up to 4
+// CTAs per SM), 2 = LMM strips of the 16/40/80-forward buckets (2 CTAs per SM).
+constexpr int kBatchClasses = 3;
 struct BatchLaunch {
     const BatchInst *insts;
-    const BatchItem *items;
-    uint32_t n_items, n_inst;
-    uint32_t *counter;
+    const BatchItem *items[kBatchClasses];
+    uint32_t n_items[kBatchClasses], n_inst;
+    uint32_t *counter;            // [kBatchClasses] ticket counters
     double *partials, *theta;
     int threads, ppt;
-    size_t smem;
+    size_t smem[kBatchClasses];
+    cudaStream_t side[kBatchClasses - 1];   // classes 1.. run on forked streams
+    cudaEvent_t fork, join[kBatchClasses - 1];
 };
 
 enum PlanKind { kPoints = 0, kProduct = 1, kCaplets = 2, kMbs = 3, kAdjoint = 4, kBatch = 5 };

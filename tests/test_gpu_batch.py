@@ -30,9 +30,9 @@ def R(tmp_path_factory):
     return rqmc
 
 
-def _oracle(seq, M, seed):
+def _oracle(seq, M, seed, insts=INSTS):
     out = []
-    for i, d in enumerate(INSTS):
+    for i, d in enumerate(insts):
         if d["kind"] == "lmm":
             lm = inputs.lmm_flat(d["n_fwd"], delta=0.25, rate=d["rate"], vol=d["vol"])
             q = O.Sequence(seq, d["n_fwd"], M, seed, inst=i, joe_kuo=JK)
@@ -62,7 +62,22 @@ def test_batch_graph_replay_is_deterministic_and_cached(R):
     b = p.execute().cpu().numpy()
     torch.cuda.synchronize()
     assert np.array_equal(a, b)
-    assert p.launches() == 3
+    # one persistent kernel per work class present (160-forward strips, MBS, smaller
+    # strips: all three here) and the theta kernel
+    assert p.launches() == 4
     assert os.path.exists(os.environ["RQMC_AUTOTUNE_CACHE"])
     parts = p.split_batch(a)
     assert [x.shape for x in parts] == [(3, d["n_fwd"] if d["kind"] == "lmm" else 1) for d in INSTS]
+
+
+@pytest.mark.parametrize("subset", [[1, 4], [0, 2, 3], [5, 6], [6, 1]])
+def test_batch_with_some_work_classes_empty(R, subset):
+    """Batches that leave one or two of the three work classes empty (MBS only, small
+    strips only, 160-forward strips only, and no small strips) still match the oracle."""
+    insts = [INSTS[k] for k in subset]
+    M, seed = 2, 3
+    got = R.price_batch(insts, M, O.SOBOL_DS, seed)
+    ref = _oracle(O.SOBOL_DS, M, seed, insts)
+    for d, g, r in zip(insts, got, ref):
+        tol = 1e-4 * np.maximum(np.abs(r), np.abs(r).max(axis=1, keepdims=True) * 1e-2) + 1e-12
+        assert np.all(np.abs(g - r) <= tol), (d, np.max(np.abs(g - r) / tol))
