@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one lmm_caplet_kernel<40, 1, float> launch
 # (Rasrap) of this workload, from an ncu capture of the kernel as committed; set to None
 # whenever that kernel changes until it is captured again.
-LMM_TRAFFIC_BYTES = 723.2e3
+LMM_TRAFFIC_BYTES = None
 
 
 def _peaks():
@@ -53,11 +53,12 @@ def lmm_algorithmic_ops(nf, nK, paths):
     MUFU: ex2 + rcp per forward update; per step lg2 (inverse CDF) and ex2 + rcp
     (fixed forward and numeraire).  Returned as SFU issue slots: on GB300 ex2 issues at
     32 per SM per clock and rcp/lg2 at 16, so an ex2 counts half a slot.
-    FP32 pipe: 5 per forward update, 16 per inverse CDF, 4 per step, 4 per strike."""
+    FP32 pipe: 4 per forward update (1 + e, drift, state), 16 per inverse CDF, 4 per step,
+    4 per strike."""
     upd = nf * (nf + 1) // 2
     n_ex2, n_rcp, n_lg2 = upd + nf, upd + nf, nf
     slots = 0.5 * n_ex2 + n_rcp + n_lg2
-    fma = 5 * upd + nf * (16 + 4 + 4 * nK)
+    fma = 4 * upd + nf * (16 + 4 + 4 * nK)
     return slots * paths, fma * paths
 
 

@@ -32,7 +32,7 @@ __host__ __device__ inline int batch_class(const BatchInst &bi) { return bi.kind
 template <int NF, int SEQ>
 __device__ __forceinline__ void batch_lmm(const BatchInst &bi, const BatchItem &it, const GenView &gv,
                                           const RedParams &r, unsigned char *smem_raw) {
-    using V2 = float2;
+    using CC = float4;
     constexpr int PAD = LmmMath<float>::PAD;
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const LmmModel<float> *md = bi.lmm;
@@ -41,14 +41,14 @@ __device__ __forceinline__ void batch_lmm(const BatchInst &bi, const BatchItem &
     size_t o_cst, o_x0, o_z, o_buf, o_acc;
     lmm_smem_layout<NF, float, P>(bi.g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
     float *zb = reinterpret_cast<float *>(smem_raw + o_z) + threadIdx.x;
-    V2 *cst = reinterpret_cast<V2 *>(smem_raw + o_cst);
+    CC *cst = reinterpret_cast<CC *>(smem_raw + o_cst);
     float *X0 = reinterpret_cast<float *>(smem_raw + o_x0);
     float *Ks = X0 + NF;
     float *wbuf = reinterpret_cast<float *>(smem_raw + o_buf) + (size_t)warp * 8 * nK * PAD;
     float *acc = reinterpret_cast<float *>(smem_raw + o_acc);
     float *cmp = acc + nw * nout;
     for (int k = threadIdx.x; k < NF; k += blockDim.x) {
-        cst[k] = V2{md->sig[k], md->cc[k]};
+        cst[k] = CC{md->sig[k], md->hc * md->sig[k], md->cc[k], 0.0f};
         X0[k] = md->X0[k];
     }
     if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md->K[threadIdx.x];

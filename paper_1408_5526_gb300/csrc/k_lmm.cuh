@@ -10,14 +10,15 @@
 // the caplet payoffs delta (L_{t+1} - K)^+ / prod_{j<=t+1}(1 + delta L_j(T_j)) are staged
 // for the warp reduction.
 //
-// Layout: the forwards live in registers as X_n = log(delta L_n) (base 2 in FP32, so one
-// step of one forward is ex2 + rcp + 5 FP32 ops).  Forward n sits in slot n-1 of an
+// Layout: the forwards live in registers as X_n = log(delta L_n) (base 2 in FP32).  Within
+// a step the drift is carried as W_n = h mu'_n + sqrt(h) Z (in log2 units), so one forward
+// costs ex2 + rcp + 4 FP32 ops: a = 1 / (1 + 2^-X), W += (h sigma_n) a, X += sigma_n W + cc_n.  Forward n sits in slot n-1 of an
 // NF-slot array (NF = 16/40/80/160).  Steps run in blocks of 8; after each block the
 // array shifts down by 8 slots, so at step tp of a block the alive slots are tp..7 of
 // group 0 (entered through an 8-way fall-through switch) plus whole groups of 8 that a
 // uniform test skips once they are dead.  The code holds NF update bodies, not NF^2/2.
-// Per-forward constants (sigma_n, -sigma_n^2 h/2) come from shared memory as one 8-byte
-// (FP32) load.  Payoffs are written to a padded per-warp transpose buffer and summed
+// Per-forward constants (sigma_n, h sigma_n, -sigma_n^2 h/2, in log2 units) come from
+// shared memory as one 16-byte (FP32) load shared by the thread's paths.  Payoffs are written to a padded per-warp transpose buffer and summed
 // once per block (lane r sums row r), then added to the warp's Kahan accumulator.
 #pragma once
 #include "paths_common.cuh"
@@ -28,41 +29,45 @@ template <typename T>
 struct LmmMath;
 // ld.shared of one forward's constants at the point of use (volatile: the compiler
 // must not hoist the 2 x NF constants of a block into registers).
+// Per-forward constants: x = sigma_n, y = h sigma_n (h in the state's log units), z = cc_n.
+struct LmmC64 {
+    double x, y, z, w;
+};
 template <>
 struct LmmMath<float> {
-    using V2 = float2;
+    using C = float4;
     static constexpr int PAD = 36;   // row stride of the transpose buffer (conflict-free 16-byte reads)
     static __device__ __forceinline__ float expb(float x) { return ex2_approx(x); }
     static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
-    static __device__ __forceinline__ float2 lds(const float2 *p) {
-        float2 v;
-        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];"
-                     : "=f"(v.x), "=f"(v.y)
+    static __device__ __forceinline__ float4 lds(const float4 *p) {
+        float4 v;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                      : "r"((unsigned)__cvta_generic_to_shared(p)));
         return v;
     }
 };
 template <>
 struct LmmMath<double> {
-    using V2 = double2;
+    using C = LmmC64;
     static constexpr int PAD = 34;
     static __device__ __forceinline__ double expb(double x) { return exp(x); }
     static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-    static __device__ __forceinline__ double2 lds(const double2 *p) {
-        double2 v;
-        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];"
-                     : "=d"(v.x), "=d"(v.y)
-                     : "r"((unsigned)__cvta_generic_to_shared(p)));
+    static __device__ __forceinline__ LmmC64 lds(const LmmC64 *p) {
+        LmmC64 v;
+        const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+        asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v.z) : "r"(a + 16));
+        v.w = 0.0;
         return v;
     }
 };
 
 template <typename T>
-__device__ __forceinline__ void lmm_update(T &X, const typename LmmMath<T>::V2 c, T &S, T hc, T Az) {
+__device__ __forceinline__ void lmm_update(T &X, const typename LmmMath<T>::C c, T &W) {
     const T a = LmmMath<T>::rcp(T(1) + LmmMath<T>::expb(-X));   // delta L / (1 + delta L), old L
-    S = fmaT(c.x, a, S);                                         // prefix including j = n
-    const T w = fmaT(S, hc, Az);
-    X = fmaT(c.x, w, X) + c.y;
+    W = fmaT(c.y, a, W);                                         // drift through j = n
+    X = fmaT(c.x, W, X) + c.z;
 }
 
 template <typename T>
@@ -93,7 +98,7 @@ __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, i
                                                            size_t *o_acc) {
     size_t off = stage_bytes(g);
     *o_cst = off;
-    off = align16(off + sizeof(typename LmmMath<T>::V2) * NF);
+    off = align16(off + sizeof(typename LmmMath<T>::C) * NF);
     *o_x0 = off;
     off = align16(off + sizeof(T) * (NF + kMaxStrikes));
     *o_z = off;
@@ -123,13 +128,13 @@ constexpr int lmm_min_blocks() {
 // load and all control flow, and give each warp P independent dependency chains.
 template <int NF, int SEQ, typename T, int P>
 __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&active)[P], const LmmScal<T> &sc,
-                                         const typename LmmMath<T>::V2 *cst, const T *X0, const T *Ks, T *zb,
+                                         const typename LmmMath<T>::C *cst, const T *X0, const T *Ks, T *zb,
                                          T *wbuf, T *wacc, T *wcmp, const int lane) {
     using M = LmmMath<T>;
-    using V2 = typename M::V2;
+    using CC = typename M::C;
     constexpr int PAD = M::PAD;
     const int nf = sc.nf, nK = sc.nK;
-    const T hc = sc.hc, sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
+    const T sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
     const int zs = P * blockDim.x;   // stride of one step in the normals buffer
     T X[P][NF];
 #pragma unroll
@@ -144,7 +149,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
     const int nblk = (nf + 7) >> 3;
     for (int b = 0; b < nblk; ++b) {
         const int ngrp = (nf - 8 * b + 7) >> 3;   // groups of 8 shifted slots still alive
-        const V2 *cb = cst + 8 * b;               // constants of original slot 8b + k
+        const CC *cb = cst + 8 * b;               // constants of original slot 8b + k
         const int nst = min(8, nf - 8 * b);
         // phase A: the block's normals (one short generator loop)
         for (int tp = 0; tp < nst; ++tp) {
@@ -153,18 +158,15 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
         }
         // phase B: forward updates and payoffs (each thread reads back its own columns)
         for (int tp = 0; tp < nst; ++tp) {
-            T Az[P], S[P];
+            T W[P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) {
-                Az[p] = sqhc * zb[tp * zs + p * blockDim.x];
-                S[p] = T(0);
-            }
+            for (int p = 0; p < P; ++p) W[p] = sqhc * zb[tp * zs + p * blockDim.x];
             // group 0: alive slots tp..7, entered through a fall-through switch
             switch (tp) {
 #define RQMC_G0(k)                                                                    \
     case (k): {                                                                       \
-        const V2 c = M::lds(cb + (k));                                                \
-        _Pragma("unroll") for (int p = 0; p < P; ++p) lmm_update<T>(X[p][(k)], c, S[p], hc, Az[p]); \
+        const CC c = M::lds(cb + (k));                                                \
+        _Pragma("unroll") for (int p = 0; p < P; ++p) lmm_update<T>(X[p][(k)], c, W[p]); \
     }
                 RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
 #undef RQMC_G0
@@ -176,9 +178,9 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
                 if (gi < ngrp) {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
-                        const V2 c = M::lds(cb + 8 * gi + k);
+                        const CC c = M::lds(cb + 8 * gi + k);
 #pragma unroll
-                        for (int p = 0; p < P; ++p) lmm_update<T>(X[p][8 * gi + k], c, S[p], hc, Az[p]);
+                        for (int p = 0; p < P; ++p) lmm_update<T>(X[p][8 * gi + k], c, W[p]);
                     }
                 }
             }
@@ -249,7 +251,7 @@ constexpr int lmm_ilp() {
 template <int NF, int SEQ, typename T>
 __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kernel(const GenParams g, const LmmModel<T> md, const RedParams r) {
     using M = LmmMath<T>;
-    using V2 = typename M::V2;
+    using CC = typename M::C;
     constexpr int PAD = M::PAD;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -258,7 +260,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     size_t o_cst, o_x0, o_z, o_buf, o_acc;
     lmm_smem_layout<NF, T, P>(g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
     T *zb = reinterpret_cast<T *>(smem_raw + o_z) + threadIdx.x;   // [8][P][blockDim], own columns
-    V2 *cst = reinterpret_cast<V2 *>(smem_raw + o_cst);
+    CC *cst = reinterpret_cast<CC *>(smem_raw + o_cst);
     T *X0 = reinterpret_cast<T *>(smem_raw + o_x0);
     T *Ks = X0 + NF;
     T *wbuf = reinterpret_cast<T *>(smem_raw + o_buf) + (size_t)warp * 8 * nK * PAD;
@@ -266,7 +268,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     T *cmp = acc + nw * nout;
     T *wacc = acc + warp * nout, *wcmp = cmp + warp * nout;
     for (int k = threadIdx.x; k < NF; k += blockDim.x) {
-        cst[k] = V2{md.sig[k], md.cc[k]};
+        cst[k] = CC{md.sig[k], md.hc * md.sig[k], md.cc[k], T(0)};
         X0[k] = md.X0[k];
     }
     if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md.K[threadIdx.x];
