@@ -153,8 +153,15 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
         const int nst = min(8, nf - 8 * b);
         // phase A: the block's normals (one short generator loop)
         for (int tp = 0; tp < nst; ++tp) {
+            if constexpr (sizeof(T) == 4) {
+                float z[P];
+                normals32<SEQ, P>(pg, 8 * b + tp, z);
 #pragma unroll
-            for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = Draw<T>::normal(pg[p], 8 * b + tp);
+                for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = z[p];
+            } else {
+#pragma unroll
+                for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = Draw<T>::normal(pg[p], 8 * b + tp);
+            }
         }
         // phase B: forward updates and payoffs (each thread reads back its own columns)
         for (int tp = 0; tp < nst; ++tp) {

@@ -88,6 +88,97 @@ struct Draw<double> {
     static __device__ __forceinline__ double normal(PathGen<SEQ> &pg, int j) { return ndtri64(pg.unif64(j)); }
 };
 
+// FP32 normals of dimension j for P paths in lockstep (the same values as P calls of
+// Draw<float>::normal).  The paths share the dimension's constants and advance together
+// through the digit or bit loop and the central inverse-CDF polynomial, so each loop
+// iteration carries P independent dependency chains instead of one.
+template <int P>
+__device__ __forceinline__ void ndtri32_lockstep(const Unif32 (&u)[P], float (&z)[P]) {
+    constexpr float C[] = RQMC_NDTRI_C;
+    float w[P], y[P], r[P];
+    bool central = true;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const float q = u[p].q;
+        const float t = 4.0f * q * (1.0f - q);
+        w[p] = -0.6931471805599453f * lg2_approx(t);
+        y[p] = fmaf(-2.0f, q, 1.0f);
+        central = central && w[p] < (float)RQMC_NDTRI_W_SPLIT;
+    }
+    if (central) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) r[p] = horner(C, w[p] - (float)RQMC_NDTRI_W_MID);
+    } else {
+#pragma unroll
+        for (int p = 0; p < P; ++p) r[p] = erfinv_ratio32(w[p]);
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        const float x = 1.4142135623730951f * y[p] * r[p];
+        z[p] = u[p].lower ? -x : x;
+    }
+}
+
+template <int SEQ, int P>
+__device__ __forceinline__ void normals32(PathGen<SEQ> (&pg)[P], int j, float (&z)[P]) {
+    Unif32 u[P];
+    const GenView &v = pg[0].v;   // every path of the thread shares the replication's view
+    if constexpr (SEQ == kPhilox) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) u[p] = unif32_from_u32(pg[p].philox_word(j));
+    } else if constexpr (SEQ == kSobolDS) {
+        // The digital construction is linear: x(n') = x(n) ^ (XOR of V_k over the set bits
+        // of n ^ n').  The first path runs the bit loop; the others differ from it in a
+        // few bits (lockstep paths are blockDim apart), so each costs a few table XORs.
+        const uint32_t *Vj = v.V + 32 * j;
+        const uint32_t n0 = (uint32_t)pg[0].n;
+        uint32_t x0 = v.shift[j];
+#pragma unroll 4
+        for (int k = 0; k < v.sob_bits; ++k) x0 ^= ((n0 >> k) & 1u) ? Vj[k] : 0u;
+        u[0] = unif32_from_u32(x0);
+#pragma unroll
+        for (int p = 1; p < P; ++p) {
+            uint32_t x = x0;
+            for (uint32_t d = (uint32_t)pg[p].n ^ n0; d != 0u; d &= d - 1u) x ^= Vj[__ffs(d) - 1];
+            u[p] = unif32_from_u32(x);
+        }
+    } else {
+        const HaltonDim &h = v.hd[j];
+        const uint16_t *sg = v.sig + h.sig_off;
+        uint32_t low[P], R[P], c[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            low[p] = h.lo0 + pg[p].i;
+            c[p] = low[p] >= h.pL ? 1u : 0u;
+            low[p] -= c[p] ? h.pL : 0u;
+            R[p] = 0u;
+        }
+        if (h.p == 2) {   // base 2: bit reversal, sigma the identity or the swap
+            const uint32_t flip = sg[0] != 0 ? (1u << h.L) - 1u : 0u;
+#pragma unroll
+            for (int p = 0; p < P; ++p) R[p] = (__brev(low[p]) >> (32u - h.L)) ^ flip;
+        } else {
+            const uint32_t pb = h.p, mg = h.magic;
+            for (uint32_t k = 0; k < h.L; ++k) {
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    uint32_t q = __umulhi(low[p], mg);
+                    uint32_t d = low[p] - q * pb;
+                    if ((int32_t)d < 0) {   // the rounded-up reciprocal overshot by one
+                        d += pb;
+                        q -= 1;
+                    }
+                    R[p] = R[p] * pb + (uint32_t)sg[d];
+                    low[p] = q;
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < P; ++p) u[p] = unif32_halton(h, R[p], c[p]);
+    }
+    ndtri32_lockstep<P>(u, z);
+}
+
 template <typename T>
 __device__ __forceinline__ T fast_exp2(T x);
 template <>
