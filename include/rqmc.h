@@ -205,7 +205,15 @@ rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double *strikes_ho
                               uint64_t seed, rqmc_precision prec, int checkpoint, rqmc_plan **plan);
 rqmc_status rqmc_plan_batch(const rqmc_instrument *inst, int n, int M, rqmc_sequence seq, uint64_t seed,
                             rqmc_precision prec, rqmc_plan **plan);
-/* Number of doubles the plan writes per execute, M*n_out.  Adjoint plans write per
+/* Point stream as a plan (the tables of rqmc_points built once): each execute writes the
+ * M*s*N coordinates of points offset..offset+N-1 to the device buffer passed as
+ * `theta_dev`, laid out [M][s][N] with the element type of rqmc_points (float for FP32,
+ * double for FP64, int64 numerators for RQMC_RAW) -- the pointer is only reinterpreted.
+ * Same argument rules and errors as rqmc_points. */
+rqmc_status rqmc_plan_points(int s, int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
+                             rqmc_precision prec, rqmc_transform tr, rqmc_plan **plan);
+/* Number of values the plan writes per execute: M*s*N coordinates for point-stream plans,
+ * otherwise M*n_out doubles.  Adjoint plans write per
  * replication [value, dV/dL_n(0) (nf), dV/dvol_n (nf), unweighted caplet values (nf*n_strikes)];
  * with all weights zero they skip the reverse sweep and act as a d-factor caplet pricer. */
 int64_t rqmc_plan_output_size(const rqmc_plan *plan);

@@ -331,6 +331,7 @@ extern "C" rqmc_status rqmc_plan_mbs(const rqmc_mbs_params *p, int64_t N, int64_
 extern "C" int64_t rqmc_plan_output_size(const rqmc_plan *plan) {
     if (!plan) return -1;
     if (plan->kind == kBatch) return batch_output_size(*plan);
+    if (plan->kind == kPoints) return (int64_t)plan->M * plan->s * (int64_t)plan->N;
     return (int64_t)plan->M * plan->nout;
 }
 
@@ -338,8 +339,8 @@ extern "C" int rqmc_plan_launches(const rqmc_plan *plan) { return plan ? plan->l
 
 extern "C" rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int paths_per_thread) {
     if (!plan) { set_error("plan is NULL"); return RQMC_EINVAL; }
-    if (plan->kind == kAdjoint || plan->kind == kBatch) {
-        set_error("adjoint and batch plans fix their launch shape when they are built");
+    if (plan->kind == kAdjoint || plan->kind == kBatch || plan->kind == kPoints) {
+        set_error("adjoint, batch and point-stream plans fix their launch shape when they are built");
         return RQMC_EUNSUPPORTED;
     }
     int t = threads > 0 ? threads : plan->threads;
@@ -361,6 +362,11 @@ extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, voi
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (plan->kind == kBatch) return batch_execute(*plan, theta_dev, st);
     cudaError_t e;
+    if (plan->kind == kPoints) {   // the buffer holds the coordinates, not theta
+        if ((e = launch_points(*plan, plan->transform, theta_dev, st)) != cudaSuccess)
+            return cuda_fail(e, "points launch");
+        return RQMC_OK;
+    }
     switch (plan->kind) {
         case kProduct: e = launch_product(*plan, st); break;
         case kCaplets: e = launch_caplets(*plan, st); break;
@@ -398,18 +404,34 @@ extern "C" rqmc_status rqmc_plan_destroy(rqmc_plan *plan) {
 }
 
 // ------------------------------------------------------------------ point stream
-extern "C" rqmc_status rqmc_points(int s, int64_t N, int M, rqmc_sequence seq, uint64_t seed, int64_t offset,
-                                   rqmc_precision prec, rqmc_transform tr, void *out, void *stream) {
-    if (!out) { set_error("out is NULL"); return RQMC_EINVAL; }
+static rqmc_status make_points_plan(int s, int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
+                                    rqmc_precision prec, rqmc_transform tr, cudaStream_t st, rqmc_plan **plan) {
     if (tr < RQMC_UNIFORM || tr > RQMC_RAW) { set_error("unknown transform"); return RQMC_EINVAL; }
     if ((int64_t)M * s * N > (int64_t(1) << 40)) { set_error("output too large"); return RQMC_EINVAL; }
     rqmc_plan *pl = nullptr;
     rqmc_status rs = new_plan(kPoints, s, N, offset, M, seq, seed, prec, &pl);
     if (rs != RQMC_OK) return rs;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    pl->transform = tr;
     rs = finish_plan(pl, {}, 16, 1, st, nullptr);
     if (rs != RQMC_OK) { destroy(pl, st); return rs; }
-    cudaError_t e = launch_points(*pl, tr, out, st);
+    pl->launches = 1;
+    *plan = pl;
+    return RQMC_OK;
+}
+
+extern "C" rqmc_status rqmc_plan_points(int s, int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
+                                        rqmc_precision prec, rqmc_transform tr, rqmc_plan **plan) {
+    return make_points_plan(s, N, offset, M, seq, seed, prec, tr, 0, plan);
+}
+
+extern "C" rqmc_status rqmc_points(int s, int64_t N, int M, rqmc_sequence seq, uint64_t seed, int64_t offset,
+                                   rqmc_precision prec, rqmc_transform tr, void *out, void *stream) {
+    if (!out) { set_error("out is NULL"); return RQMC_EINVAL; }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    rqmc_plan *pl = nullptr;
+    rqmc_status rs = make_points_plan(s, N, offset, M, seq, seed, prec, tr, st, &pl);
+    if (rs != RQMC_OK) return rs;
+    cudaError_t e = launch_points(*pl, pl->transform, out, st);
     destroy(pl, st);   // stream-ordered free after the kernel
     if (e != cudaSuccess) return cuda_fail(e, "points launch");
     return RQMC_OK;

@@ -2,7 +2,8 @@
 // layout out[(m*s + j)*N + i] (the generator-throughput setting of Sec. 4, Table 2).
 // Rows (m, j) are cut into chunks of ITEMS*blockDim consecutive points; a thread writes
 // ITEMS coordinates blockDim apart so every warp store is one contiguous 128-byte (FP32)
-// segment.  Philox rows come four dimensions at a time from one counter.
+// segment, and computes them in lockstep (shared digit / bit loop and inverse-CDF
+// polynomial).  Philox rows come four dimensions at a time from one counter.
 #include "paths_common.cuh"
 
 namespace rqmc {
@@ -18,22 +19,6 @@ __device__ __forceinline__ T value_from_u32(uint32_t x) {
         else return v.lower ? v.q : 1.0f - v.q;
     } else {
         const Unif64 v = unif64_from_u32(x);
-        if constexpr (TR == RQMC_NORMAL) return ndtri64(v);
-        else return v.lower ? v.q : 1.0 - v.q;
-    }
-}
-
-template <int TR, typename T>
-__device__ __forceinline__ T halton_value(const HaltonDim &h, const uint16_t *sig, uint32_t i) {
-    uint32_t c;
-    const uint32_t R = halton_R(h, sig, i, c);
-    if constexpr (TR == RQMC_RAW) return (T)halton_num(h, R, c);
-    else if constexpr (sizeof(T) == 4) {
-        const Unif32 v = unif32_halton(h, R, c);
-        if constexpr (TR == RQMC_NORMAL) return ndtri32(v);
-        else return v.lower ? v.q : 1.0f - v.q;
-    } else {
-        const Unif64 v = unif64_halton(h, R, c);
         if constexpr (TR == RQMC_NORMAL) return ndtri64(v);
         else return v.lower ? v.q : 1.0 - v.q;
     }
@@ -65,25 +50,70 @@ __global__ void __launch_bounds__(256) points_kernel(const GenParams g, uint32_t
                 }
             }
         } else {
+            // Halton / Sobol' rows: the ITEMS points of the thread advance in lockstep
             const int m = (int)(row / g.s), j = (int)(row % g.s);
             T *dst = out + row * N;
+            if (base >= N) continue;
+            uint32_t ii[kPtItems];
+            bool ok[kPtItems];
+#pragma unroll
+            for (int it = 0; it < kPtItems; ++it) {
+                const uint32_t i = base + it * blockDim.x;
+                ok[it] = i < N;
+                ii[it] = ok[it] ? i : base;   // past the end: recompute a valid point, store nothing
+            }
             if (g.seq == kSobolDS) {
-                const uint32_t *V = g.sobV + 32 * j;
-                const uint32_t sh = __ldg(g.sobShift + row);
-#pragma unroll 4
-                for (int it = 0; it < kPtItems; ++it) {
-                    const uint32_t i = base + it * blockDim.x;
-                    if (i >= N) break;
-                    dst[i] = value_from_u32<TR, T>(sobol_x(V, sh, (uint32_t)(g.offset + i), g.sob_bits));
+                uint32_t n[kPtItems], x[kPtItems];
+#pragma unroll
+                for (int it = 0; it < kPtItems; ++it) n[it] = (uint32_t)(g.offset + ii[it]);
+                sobol_lockstep<kPtItems>(g.sobV + 32 * j, __ldg(g.sobShift + row), n, g.sob_bits, x);
+                if constexpr (TR == RQMC_NORMAL && sizeof(T) == 4) {
+                    Unif32 u[kPtItems];
+                    float z[kPtItems];
+#pragma unroll
+                    for (int it = 0; it < kPtItems; ++it) u[it] = unif32_from_u32(x[it]);
+                    ndtri32_lockstep<kPtItems>(u, z);
+#pragma unroll
+                    for (int it = 0; it < kPtItems; ++it)
+                        if (ok[it]) dst[ii[it]] = z[it];
+                } else {
+#pragma unroll
+                    for (int it = 0; it < kPtItems; ++it)
+                        if (ok[it]) dst[ii[it]] = value_from_u32<TR, T>(x[it]);
                 }
             } else {
-                const HaltonDim h = g.hdim[row];
+                const HaltonDim h = g.hdim[row];   // one copy in registers, shared by the items
                 const uint16_t *sig = g.sigma + (size_t)m * g.sig_len;
-#pragma unroll 4
-                for (int it = 0; it < kPtItems; ++it) {
-                    const uint32_t i = base + it * blockDim.x;
-                    if (i >= N) break;
-                    dst[i] = halton_value<TR, T>(h, sig, i);
+                uint32_t R[kPtItems], c[kPtItems];
+                halton_R_lockstep<kPtItems>(h, sig + h.sig_off, ii, R, c);
+                if constexpr (TR == RQMC_RAW) {
+#pragma unroll
+                    for (int it = 0; it < kPtItems; ++it)
+                        if (ok[it]) dst[ii[it]] = (T)halton_num(h, R[it], c[it]);
+                } else if constexpr (sizeof(T) == 4) {
+                    Unif32 u[kPtItems];
+#pragma unroll
+                    for (int it = 0; it < kPtItems; ++it) u[it] = unif32_halton(h, R[it], c[it]);
+                    if constexpr (TR == RQMC_NORMAL) {
+                        float z[kPtItems];
+                        ndtri32_lockstep<kPtItems>(u, z);
+#pragma unroll
+                        for (int it = 0; it < kPtItems; ++it)
+                            if (ok[it]) dst[ii[it]] = z[it];
+                    } else {
+#pragma unroll
+                        for (int it = 0; it < kPtItems; ++it)
+                            if (ok[it]) dst[ii[it]] = u[it].lower ? u[it].q : 1.0f - u[it].q;
+                    }
+                } else {
+#pragma unroll
+                    for (int it = 0; it < kPtItems; ++it) {
+                        const Unif64 v = unif64_halton(h, R[it], c[it]);
+                        T val;
+                        if constexpr (TR == RQMC_NORMAL) val = ndtri64(v);
+                        else val = v.lower ? v.q : 1.0 - v.q;
+                        if (ok[it]) dst[ii[it]] = val;
+                    }
                 }
             }
         }

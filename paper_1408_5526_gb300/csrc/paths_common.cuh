@@ -88,10 +88,66 @@ struct Draw<double> {
     static __device__ __forceinline__ double normal(PathGen<SEQ> &pg, int j) { return ndtri64(pg.unif64(j)); }
 };
 
-// FP32 normals of dimension j for P paths in lockstep (the same values as P calls of
-// Draw<float>::normal).  The paths share the dimension's constants and advance together
-// through the digit or bit loop and the central inverse-CDF polynomial, so each loop
-// iteration carries P independent dependency chains instead of one.
+// ------------------------------------------------------------------ lockstep generation
+// P coordinates of one dimension at once (P paths of a thread, or P points of a stream):
+// they share the dimension's constants and advance together through the digit or bit loop
+// and the inverse-CDF polynomial, so each loop iteration carries P independent dependency
+// chains.  Every value is bit-identical to the one-at-a-time routines.
+
+// Halton/Rasrap: R and carry of the points lo0 + i[p] (see halton_R); sg = sigma of the dim.
+template <int P>
+__device__ __forceinline__ void halton_R_lockstep(const HaltonDim &h, const uint16_t *__restrict__ sg,
+                                                  const uint32_t (&i)[P], uint32_t (&R)[P], uint32_t (&c)[P]) {
+    uint32_t low[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        low[p] = h.lo0 + i[p];
+        c[p] = low[p] >= h.pL ? 1u : 0u;
+        low[p] -= c[p] ? h.pL : 0u;
+        R[p] = 0u;
+    }
+    if (h.p == 2) {   // base 2: bit reversal, sigma the identity or the swap
+        const uint32_t flip = sg[0] != 0 ? (1u << h.L) - 1u : 0u;
+#pragma unroll
+        for (int p = 0; p < P; ++p) R[p] = (__brev(low[p]) >> (32u - h.L)) ^ flip;
+        return;
+    }
+    const uint32_t pb = h.p, mg = h.magic;
+    for (uint32_t k = 0; k < h.L; ++k) {
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            uint32_t q = __umulhi(low[p], mg);
+            uint32_t d = low[p] - q * pb;
+            if ((int32_t)d < 0) {   // the rounded-up reciprocal overshot by one
+                d += pb;
+                q -= 1;
+            }
+            R[p] = R[p] * pb + (uint32_t)sg[d];
+            low[p] = q;
+        }
+    }
+}
+
+// Sobol': x = shift ^ XOR of V_k over the set bits of n[p].  The construction is linear,
+// x(n') = x(n) ^ (XOR of V_k over the set bits of n ^ n'): the first point runs the bit
+// loop, the others (a fixed stride apart) differ from it in a few bits and cost a few XORs.
+template <int P>
+__device__ __forceinline__ void sobol_lockstep(const uint32_t *__restrict__ Vj, uint32_t shift,
+                                               const uint32_t (&n)[P], int bits, uint32_t (&x)[P]) {
+    uint32_t x0 = shift;
+#pragma unroll 4
+    for (int k = 0; k < bits; ++k) x0 ^= ((n[0] >> k) & 1u) ? Vj[k] : 0u;
+    x[0] = x0;
+#pragma unroll
+    for (int p = 1; p < P; ++p) {
+        uint32_t xp = x0;
+        for (uint32_t d = n[p] ^ n[0]; d != 0u; d &= d - 1u) xp ^= Vj[__ffs(d) - 1];
+        x[p] = xp;
+    }
+}
+
+// Phi^-1 of P uniforms: the central polynomial for all of them in straight-line code, the
+// tail branches only where some value needs them (about 0.3 % of the values).
 template <int P>
 __device__ __forceinline__ void ndtri32_lockstep(const Unif32 (&u)[P], float (&z)[P]) {
     constexpr float C[] = RQMC_NDTRI_C;
@@ -104,13 +160,12 @@ __device__ __forceinline__ void ndtri32_lockstep(const Unif32 (&u)[P], float (&z
         w[p] = -0.6931471805599453f * lg2_approx(t);
         y[p] = fmaf(-2.0f, q, 1.0f);
         central = central && w[p] < (float)RQMC_NDTRI_W_SPLIT;
+        r[p] = horner(C, w[p] - (float)RQMC_NDTRI_W_MID);
     }
-    if (central) {
+    if (!central) {
 #pragma unroll
-        for (int p = 0; p < P; ++p) r[p] = horner(C, w[p] - (float)RQMC_NDTRI_W_MID);
-    } else {
-#pragma unroll
-        for (int p = 0; p < P; ++p) r[p] = erfinv_ratio32(w[p]);
+        for (int p = 0; p < P; ++p)
+            if (w[p] >= (float)RQMC_NDTRI_W_SPLIT) r[p] = erfinv_ratio32(w[p]);
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
@@ -119,6 +174,8 @@ __device__ __forceinline__ void ndtri32_lockstep(const Unif32 (&u)[P], float (&z
     }
 }
 
+// FP32 normals of dimension j for the P lockstep paths of a thread (the values of P calls
+// of Draw<float>::normal).
 template <int SEQ, int P>
 __device__ __forceinline__ void normals32(PathGen<SEQ> (&pg)[P], int j, float (&z)[P]) {
     Unif32 u[P];
@@ -127,52 +184,18 @@ __device__ __forceinline__ void normals32(PathGen<SEQ> (&pg)[P], int j, float (&
 #pragma unroll
         for (int p = 0; p < P; ++p) u[p] = unif32_from_u32(pg[p].philox_word(j));
     } else if constexpr (SEQ == kSobolDS) {
-        // The digital construction is linear: x(n') = x(n) ^ (XOR of V_k over the set bits
-        // of n ^ n').  The first path runs the bit loop; the others differ from it in a
-        // few bits (lockstep paths are blockDim apart), so each costs a few table XORs.
-        const uint32_t *Vj = v.V + 32 * j;
-        const uint32_t n0 = (uint32_t)pg[0].n;
-        uint32_t x0 = v.shift[j];
-#pragma unroll 4
-        for (int k = 0; k < v.sob_bits; ++k) x0 ^= ((n0 >> k) & 1u) ? Vj[k] : 0u;
-        u[0] = unif32_from_u32(x0);
+        uint32_t n[P], x[P];
 #pragma unroll
-        for (int p = 1; p < P; ++p) {
-            uint32_t x = x0;
-            for (uint32_t d = (uint32_t)pg[p].n ^ n0; d != 0u; d &= d - 1u) x ^= Vj[__ffs(d) - 1];
-            u[p] = unif32_from_u32(x);
-        }
+        for (int p = 0; p < P; ++p) n[p] = (uint32_t)pg[p].n;
+        sobol_lockstep<P>(v.V + 32 * j, v.shift[j], n, v.sob_bits, x);
+#pragma unroll
+        for (int p = 0; p < P; ++p) u[p] = unif32_from_u32(x[p]);
     } else {
         const HaltonDim &h = v.hd[j];
-        const uint16_t *sg = v.sig + h.sig_off;
-        uint32_t low[P], R[P], c[P];
+        uint32_t i[P], R[P], c[P];
 #pragma unroll
-        for (int p = 0; p < P; ++p) {
-            low[p] = h.lo0 + pg[p].i;
-            c[p] = low[p] >= h.pL ? 1u : 0u;
-            low[p] -= c[p] ? h.pL : 0u;
-            R[p] = 0u;
-        }
-        if (h.p == 2) {   // base 2: bit reversal, sigma the identity or the swap
-            const uint32_t flip = sg[0] != 0 ? (1u << h.L) - 1u : 0u;
-#pragma unroll
-            for (int p = 0; p < P; ++p) R[p] = (__brev(low[p]) >> (32u - h.L)) ^ flip;
-        } else {
-            const uint32_t pb = h.p, mg = h.magic;
-            for (uint32_t k = 0; k < h.L; ++k) {
-#pragma unroll
-                for (int p = 0; p < P; ++p) {
-                    uint32_t q = __umulhi(low[p], mg);
-                    uint32_t d = low[p] - q * pb;
-                    if ((int32_t)d < 0) {   // the rounded-up reciprocal overshot by one
-                        d += pb;
-                        q -= 1;
-                    }
-                    R[p] = R[p] * pb + (uint32_t)sg[d];
-                    low[p] = q;
-                }
-            }
-        }
+        for (int p = 0; p < P; ++p) i[p] = pg[p].i;
+        halton_R_lockstep<P>(h, v.sig + h.sig_off, i, R, c);
 #pragma unroll
         for (int p = 0; p < P; ++p) u[p] = unif32_halton(h, R[p], c[p]);
     }

@@ -143,6 +143,7 @@ struct Plan {
     RedParams red{};
     int threads = 256, ppt = 4, grid = 0;
     int nf_bucket = 0;
+    int transform = 0;       // point-stream plans: RQMC_UNIFORM / RQMC_NORMAL / RQMC_RAW
     int launches = 0;
     // device memory (one allocation)
     void *d_buf = nullptr;

@@ -33,7 +33,8 @@ EXPORTS = ["rqmc_set_sobol_table", "rqmc_points", "rqmc_integrate_product", "pri
            "price_adjoint", "price_batch", "rqmc_plan_product", "rqmc_plan_caplets", "rqmc_plan_mbs",
            "rqmc_plan_adjoint", "rqmc_plan_batch", "rqmc_plan_output_size", "rqmc_plan_launches",
            "rqmc_plan_set_launch", "rqmc_plan_execute", "rqmc_plan_check", "rqmc_plan_destroy",
-           "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version", "rqmc_price_caplets_noalloc"]
+           "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version", "rqmc_price_caplets_noalloc",
+           "rqmc_plan_points"]
 
 
 class RqmcError(RuntimeError):
@@ -93,6 +94,7 @@ def load(path: str = LIB_PATH):
         L.rqmc_plan_adjoint.argtypes = [C.POINTER(LmmParams), dp, C.c_int, dp, i64, i64, C.c_int, C.c_int,
                                         C.c_uint64, C.c_int, C.c_int, pp]
         L.rqmc_plan_batch.argtypes = [C.POINTER(Instrument), C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, pp]
+        L.rqmc_plan_points.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, pp]
         L.rqmc_plan_output_size.argtypes = [vp]
         L.rqmc_plan_output_size.restype = i64
         L.rqmc_plan_launches.argtypes = [vp]
@@ -277,6 +279,19 @@ class Plan:
         self.nout = nout
 
     @classmethod
+    def points(cls, s, N, M, seq, seed, prec="fp32", transform="uniform", offset=0):
+        """Point stream: execute(out) fills out [M, s, N] (float32 / float64, int64 for raw)."""
+        L = load()
+        h = C.c_void_p()
+        tr = _enum(transform, _TR)
+        pr = _enum(prec, _PREC)
+        _check(L, L.rqmc_plan_points(s, N, offset, M, _enum(seq, _SEQ), seed, pr, tr, C.byref(h)))
+        pl = cls(h, M, 0)
+        pl.points_shape = (M, s, N)
+        pl.points_dtype = "int64" if tr == RAW else ("float32" if pr == FP32 else "float64")
+        return pl
+
+    @classmethod
     def product(cls, s, N, M, seq, seed, a, prec="fp64", offset=0):
         L = load()
         a = np.ascontiguousarray(a, dtype=np.float64)
@@ -345,7 +360,10 @@ class Plan:
     def execute(self, theta=None, stream=None):
         import torch
         if theta is None:
-            theta = torch.empty(self.output_size(), dtype=torch.float64, device="cuda")
+            if hasattr(self, "points_shape"):
+                theta = torch.empty(self.points_shape, dtype=getattr(torch, self.points_dtype), device="cuda")
+            else:
+                theta = torch.empty(self.output_size(), dtype=torch.float64, device="cuda")
         L = load()
         _check(L, L.rqmc_plan_execute(self._h, C.cast(C.c_void_p(theta.data_ptr()), C.POINTER(C.c_double)),
                                       _stream(stream)))

@@ -39,6 +39,21 @@ def test_points_raw_bit_exact(R, seq, s, offset):
     assert np.array_equal(gpu, ora)
 
 
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX])
+@pytest.mark.parametrize("prec,transform", [("fp32", "normal"), ("fp64", "uniform"), ("fp32", "raw")])
+def test_points_plan_matches_one_shot(R, seq, prec, transform):
+    """The point-stream plan (tables built once) writes exactly what rqmc_points writes,
+    on every execute, with a point offset."""
+    N, M, s, off = 2049, 2, 24, 777
+    ref = _to_np(R.rqmc_points(s, N, M, seq, 9, offset=off, prec=prec, transform=transform))
+    p = R.Plan.points(s, N, M, seq, 9, prec=prec, transform=transform, offset=off)
+    assert p.output_size() == M * s * N and p.launches() == 1
+    a = _to_np(p.execute())
+    b = _to_np(p.execute())
+    p.close()
+    assert a.shape == ref.shape and np.array_equal(a, ref) and np.array_equal(b, ref)
+
+
 @pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX])
 def test_points_fp64_uniform_and_normal(R, seq):
     N, M, s = 2500, 2, 16
