@@ -16,15 +16,13 @@ namespace rqmc {
 
 // Paths per thread in lockstep per bucket, sized to the register budget of the bucket's
 // work class (16/40/80 forwards: 2 CTAs per SM, 128 registers; 160: 1 CTA per SM).  MBS
-// paths stay one per thread: their month is dominated by the branches of the inverse CDF
-// and the arctangent, which keep the compiler from interleaving paths, so lockstep copies
-// only add code (4 and 8 paths measured 18 % slower than 1 on the 128 MBS of the
-// 512-instrument batch).
+// paths go two per thread, as in the MBS kernel: their coordinates and the central
+// inverse-CDF branch are generated together.
 template <int NF>
 __host__ __device__ constexpr int batch_ilp() {
     return NF <= 16 ? 4 : NF <= 40 ? 2 : 1;
 }
-constexpr int kBatchMbsIlp = 1;
+constexpr int kBatchMbsIlp = 2;
 
 // Work class of an instrument (see BatchLaunch).
 __host__ __device__ inline int batch_class(const BatchInst &bi) { return bi.kind != 0 ? 1 : bi.bucket == 160 ? 0 : 2; }

@@ -9,8 +9,16 @@
 
 namespace rqmc {
 
+// Paths per thread in lockstep: two in FP32 (their coordinates share the dimension's
+// constants, and a Sobol' point blockDim away costs a few XORs), one in FP64.
+template <typename T>
+constexpr int mbs_ilp() {
+    return sizeof(T) == 4 ? 2 : 1;
+}
+
 template <typename T, int SEQ>
 __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsModel<T> md, const RedParams r) {
+    constexpr int P = mbs_ilp<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *acc = reinterpret_cast<T *>(smem_raw + stage_bytes(g));
@@ -31,15 +39,22 @@ __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsMo
             staged_m = m;
         }
         __syncthreads();
-        for (int pp = 0; pp < r.ppt; ++pp) {
-            const uint32_t i = tile * r.tile + (uint32_t)(pp * blockDim.x + threadIdx.x);
-            const bool active = i < r.N;
-            if (!__any_sync(0xffffffffu, active)) break;
-            PathGen<SEQ> pg[1];
-            pg[0].init(gv, active ? i : 0u);
-            T v[1];
-            mbs_paths<T, SEQ, 1>(pg, md, ck, v);
-            warp_accumulate<T>(active ? v[0] : T(0), acc + warp, cmp + warp, 0, lane);
+        for (int pp = 0; pp < r.ppt; pp += P) {
+            PathGen<SEQ> pg[P];
+            bool act[P];
+            bool any = false;
+#pragma unroll
+            for (int p = 0; p < P; ++p) {
+                const uint32_t i = tile * r.tile + (uint32_t)((pp + p) * blockDim.x + threadIdx.x);
+                act[p] = pp + p < r.ppt && i < r.N;
+                any = any || act[p];
+                pg[p].init(gv, act[p] ? i : 0u);
+            }
+            if (!__any_sync(0xffffffffu, any)) break;
+            T v[P];
+            mbs_paths<T, SEQ, P>(pg, md, ck, v);
+#pragma unroll
+            for (int p = 0; p < P; ++p) warp_accumulate<T>(act[p] ? v[p] : T(0), acc + warp, cmp + warp, 0, lane);
         }
         flush_unit(r, u, acc, cmp);
     }

@@ -31,9 +31,16 @@ __device__ __forceinline__ void mbs_paths(PathGen<SEQ> (&pg)[P], const MbsModel<
     }
     for (int k = 1; k <= md.months; ++k) {
         const T c = ck[k];
+        T zs[P];
+        if constexpr (sizeof(T) == 4) {
+            normals32<SEQ, P>(pg, k - 1, zs);   // the P paths' normals of month k together
+        } else {
+#pragma unroll
+            for (int p = 0; p < P; ++p) zs[p] = Draw<T>::normal(pg[p], k - 1);
+        }
 #pragma unroll
         for (int p = 0; p < P; ++p) {
-            const T z = Draw<T>::normal(pg[p], k - 1);
+            const T z = zs[p];
             const T ik = ip[p] * mbs_exp<T>(fmaT(md.sz, z, md.lk0));
             const T w = fmaT(md.K2, mbs_atan(fmaT(md.K3, ik, md.K4)), md.K1);
             const T mk = md.c * rr[p] * ((T(1) - w) + w * c);
