@@ -268,7 +268,8 @@ def other_workloads(args, dev, seed):
     """The other configurations of the scope, one timed figure each (median of a few
     launches, L2 flushed before each, inputs resident): product integrand (FP64),
     LMM caplets in FP64, MBS (FP32), two-factor adjoint Greeks (FP32), the
-    512-instrument batch (FP32, graph launch) and the point stream (HBM write GB/s)."""
+    512-instrument batch (FP32, graph launch), the Treasury-curve study of Sec. 5 (std, time
+    and efficiency against N) and the point stream (HBM write GB/s)."""
     import torch
     from paper_1408_5526_gb300 import inputs, rqmc
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
@@ -316,6 +317,26 @@ def other_workloads(args, dev, seed):
     steps = sum(d["N"] * 32 * (d["n_fwd"] if d["kind"] == "lmm" else d["months"]) for d in desc)
     out["batch_512_M32_fp32_sobol"] = {"ms": ms, "path_steps_per_s": steps / (ms / 1e3), "path_steps": steps}
     p.close()
+    # Sec. 5's Treasury-curve study: caplet on L_10 (T = 5, delta = 0.5, K = 1 %, sigma = 4 %)
+    # from the 24 Feb 2012 curve; std of M = 100 independent estimates, time and efficiency
+    # (std x time) against N, and the fitted convergence rate of the std
+    st = inputs.TREASURY_STUDY
+    lmt = inputs.lmm_treasury(st["T"], st["delta"], st["vol"])
+    study = {}
+    for s_ in SEQS:
+        rows = []
+        for e in range(10, 21, 2):
+            pt = rqmc.Plan.caplets(lmt, [st["K"]], 1 << e, st["M"], s_, seed, prec="fp32")
+            ot = torch.empty(pt.output_size(), dtype=torch.float64, device=dev)
+            ms = _time_plan(lambda: pt.execute(ot), 3, flush)
+            th = ot.cpu().numpy().reshape(st["M"], -1)[:, lmt["n_fwd"] - 1]
+            pt.close()
+            rows.append({"N": 1 << e, "rq": float(th.mean()), "std": float(th.std(ddof=1)), "ms": ms,
+                         "efficiency": float(th.std(ddof=1)) * ms})
+        lx = np.log([r["N"] for r in rows])
+        ly = np.log([r["std"] for r in rows])
+        study[s_] = {"rate": float(np.polyfit(lx, ly, 1)[0]), "by_N": rows}
+    out["lmm_treasury_study_T5_M100_fp32"] = study
     # point stream: s = 360, N = 65536, M = 64 FP32 normals, written to HBM
     buf = torch.empty((M_REPL, 360, N_PATHS), dtype=torch.float32, device=dev)
     res = {}

@@ -109,6 +109,30 @@ TREASURY_2012_02_24 = {   # Table 3: maturity in years -> yield in percent
     30: 3.10}
 
 
+def treasury_bonds(n: int, delta: float = 0.5, table: dict = TREASURY_2012_02_24) -> np.ndarray:
+    """Bond prices B_0(0) = 1, B_1(0), ..., B_n(0) at T_k = k delta from the Treasury yields of
+    Table 3: a natural cubic spline through (maturity, yield), evaluated every delta years,
+    read as bond-equivalent (semiannual) yields, B(T) = (1 + y(T)/2)^(-2T)."""
+    from scipy.interpolate import CubicSpline
+    mats = np.array(sorted(table), dtype=np.float64)
+    ys = np.array([table[m] for m in sorted(table)], dtype=np.float64) / 100.0
+    spline = CubicSpline(mats, ys, bc_type="natural")
+    t = delta * np.arange(1, n + 1)
+    B = (1.0 + spline(t) / 2.0) ** (-2.0 * t)
+    return np.concatenate([[1.0], B])
+
+
+def lmm_treasury(T: float = 5.0, delta: float = 0.5, vol: float = 0.04) -> dict:
+    """The Treasury-curve LMM study of Sec. 5: forwards L_0..L_nf (nf = T / delta) from the
+    24 Feb 2012 curve (eq. BL), flat vol; the caplet of the study is the one on L_nf, fixed
+    at T and paid at T + delta, with strike 1 %."""
+    nf = int(round(T / delta))
+    return lmm_from_bonds(treasury_bonds(nf + 1, delta), delta, vol)
+
+
+TREASURY_STUDY = {"T": 5.0, "delta": 0.5, "K": 0.01, "vol": 0.04, "M": 100}
+
+
 # ---------------------------------------------------------------- batch
 def batch_instruments(seed: int = 1, n_lmm: int = 384, n_mbs: int = 128) -> list:
     """512 heterogeneous instruments: LMM caplet strips with 8..160 quarterly

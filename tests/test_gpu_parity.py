@@ -121,6 +121,21 @@ def test_caplets_small(R, seq):
     assert np.all(np.abs(th32 - th_o) <= _caplet_tol(th_o, len(K)))
 
 
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX])
+def test_caplets_treasury_curve(R, seq):
+    """Sec. 5's Treasury-curve study inputs (non-flat curve, delta = 0.5, sigma = 4 %,
+    K = 1 %) against the oracle in FP64 and FP32."""
+    st = inputs.TREASURY_STUDY
+    lm = inputs.lmm_treasury(st["T"], st["delta"], st["vol"])
+    K = np.array([st["K"]])
+    N, M = 3000, 3
+    th_o = O.lmm_caplets(O.Sequence(seq, lm["n_fwd"], M, 5, joe_kuo=JK), lm, K, N)
+    th64, _, _ = R.price_caplets(lm, K, N, M, seq, 5, prec="fp64")
+    np.testing.assert_allclose(th64, th_o, rtol=1e-11, atol=1e-15)
+    th32, _, _ = R.price_caplets(lm, K, N, M, seq, 5, prec="fp32")
+    assert np.all(np.abs(th32 - th_o) <= 1e-4 * np.abs(th_o) + 1e-9)
+
+
 @pytest.mark.parametrize("nf", [1, 7, 16, 23, 80, 160])
 def test_caplets_bucket_edges(R, nf):
     lm = inputs.lmm_flat(nf, vol=0.2)

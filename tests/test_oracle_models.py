@@ -143,6 +143,40 @@ def test_lmm_black_formula_within_discretization_budget():
             assert abs(rq1[o] - black) < 0.01 * black + 2e-7
 
 
+def test_treasury_curve_inputs_reproduce_table_3():
+    # the spline passes through the table: at 6 months, 1, 2, 3 and 5 years the bond prices
+    # are exactly the bond-equivalent discount factors of the quoted yields
+    B = inputs.treasury_bonds(10, 0.5)
+    for T, y in ((0.5, 0.14), (1.0, 0.18), (2.0, 0.31), (3.0, 0.43), (5.0, 0.89)):
+        k = int(round(T / 0.5))
+        assert abs(B[k] - (1 + y / 200.0) ** (-2 * T)) < 1e-15
+    lm = inputs.lmm_treasury()
+    assert lm["n_fwd"] == 10 and len(lm["L0"]) == 11
+    # eq. BL inverted: the forwards rebuild the bond prices
+    Bn = np.concatenate([[1.0], np.cumprod(1.0 / (1.0 + 0.5 * lm["L0"]))])
+    np.testing.assert_allclose(Bn, inputs.treasury_bonds(11, 0.5), rtol=1e-14)
+
+
+def test_treasury_study_caplet_matches_black():
+    # Sec. 5's study, (t, T, delta, K, sigma) = (0, 5, 0.5, 0.01, 0.04): the caplet on L_10
+    # against Black on the same initial curve, within the measured discretization budget
+    st = inputs.TREASURY_STUDY
+    lm1 = inputs.lmm_treasury(st["T"], st["delta"], st["vol"])
+    lm2 = dict(lm1, substeps=2)
+    nf = lm1["n_fwd"]
+    M, N = 16, 8192
+    q1 = O.Sequence(O.SOBOL_DS, nf, M, 2, joe_kuo=JK)
+    q2 = O.Sequence(O.SOBOL_DS, 2 * nf, M, 2, joe_kuo=JK)
+    rq1, sd1 = O.rq_stats(O.lmm_caplets(q1, lm1, [st["K"]], N))
+    rq2, sd2 = O.rq_stats(O.lmm_caplets(q2, lm2, [st["K"]], N))
+    B = inputs.treasury_bonds(nf + 1, st["delta"])
+    for n in (1, 5, nf):
+        black = st["delta"] * _black(lm1["L0"][n], st["K"], st["vol"], n * st["delta"], B[n + 1])
+        o = n - 1
+        budget = 3 * (sd1[o] + sd2[o]) / math.sqrt(M) + 3 * abs(rq1[o] - rq2[o]) + 1e-9
+        assert abs(rq1[o] - black) <= budget, (n, rq1[o], rq2[o], black)
+
+
 # ------------------------------------------------------------------ MBS
 def _mbs_deterministic(mb):
     Mm, i0 = mb["months"], mb["i0"]
