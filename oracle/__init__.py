@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-HALTON_RS, RASRAP, SOBOL_DS, PHILOX = 0, 1, 2, 3
+HALTON_RS, RASRAP, SOBOL_DS, PHILOX, SOBOL_LMS = 0, 1, 2, 3, 4
 UNIFORM, NORMAL, RAW = 0, 1, 2
 
 
@@ -74,6 +74,10 @@ def lib():
         L.orc_sobol_binary.argtypes = [u32p, C.c_uint64]
         L.orc_sobol_binary.restype = C.c_uint32
         L.orc_sobol_shift.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_int]
+        L.orc_sobol_lms_rows.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_int, u32p]
+        L.orc_sobol_lms_rows.restype = None
+        L.orc_sobol_lms_apply.argtypes = [u32p, C.c_uint32]
+        L.orc_sobol_lms_apply.restype = C.c_uint32
         L.orc_sobol_shift.restype = C.c_uint32
         L.orc_philox_path_word.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_uint64]
         L.orc_philox_path_word.restype = C.c_uint32
@@ -163,6 +167,10 @@ def sobol_binary(Vj, n: int) -> int:
     return int(lib().orc_sobol_binary(_p(v, C.c_uint32), n))
 
 
+def sobol_shift(seed: int, inst: int, m: int, j: int) -> int:
+    return int(lib().orc_sobol_shift(seed, inst, m, j))
+
+
 def ndtri_lower(q: float) -> float:
     return float(lib().orc_ndtri_lower(q))
 
@@ -178,7 +186,7 @@ class Sequence:
 
     def __init__(self, seq: int, s: int, M: int, seed: int, inst: int = 0, joe_kuo=None):
         self.seq, self.s, self.M, self.seed, self.inst = seq, s, M, seed, inst
-        if seq == SOBOL_DS:
+        if seq in (SOBOL_DS, SOBOL_LMS):
             if joe_kuo is None:
                 raise ValueError("Sobol' needs the Joe-Kuo table (poly, vinit)")
             poly = np.ascontiguousarray(joe_kuo[0][:s], dtype=np.int64)

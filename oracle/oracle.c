@@ -70,7 +70,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 
 /* Counter layout (reading c17): key = (seed_lo, seed_hi); word 3 of the
  * counter carries a tag in its low 8 bits and the instrument index above. */
-enum { ORC_TAG_PATH = 0, ORC_TAG_START = 1, ORC_TAG_PERM = 2, ORC_TAG_SHIFT = 3 };
+enum { ORC_TAG_PATH = 0, ORC_TAG_START = 1, ORC_TAG_PERM = 2, ORC_TAG_SHIFT = 3, ORC_TAG_SCRAMBLE = 4 };
 
 static void orc_philox_call(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                             uint32_t tag, uint32_t inst, uint32_t out[4])
@@ -238,10 +238,40 @@ uint32_t orc_sobol_shift(uint64_t seed, uint32_t inst, int m, int j)
     return w[0];
 }
 
+/* Matousek's random linear scrambling (Sec. 3.2; reading c23): a random  */
+/* nonsingular lower-triangular binary matrix L_{m,j} acts on the binary  */
+/* digits (most significant first) of every coordinate, y = L x, before   */
+/* the digital shift.  Row r (output digit r, r = 0..31) is stored as a   */
+/* 32-bit mask over the input digits (digit l = bit 31 - l): the diagonal */
+/* is 1, and the r entries left of it are the top r bits of Philox word   */
+/* r - 1 of the counters (j, (r-1)/4, m, tag 4).                          */
+void orc_sobol_lms_rows(uint64_t seed, uint32_t inst, int m, int j, uint32_t rows[32])
+{
+    rows[0] = 0x80000000u;
+    for (int r = 1; r < 32; ++r) {
+        uint32_t w[4];
+        orc_philox_call(seed, (uint32_t)j, (uint32_t)((r - 1) >> 2), (uint32_t)m, ORC_TAG_SCRAMBLE, inst, w);
+        const uint32_t word = w[(r - 1) & 3];
+        rows[r] = ((word >> (32 - r)) << (32 - r)) | (0x80000000u >> r);
+    }
+}
+
+/* y = L x over GF(2): output digit r is the parity of row r and x. */
+uint32_t orc_sobol_lms_apply(const uint32_t rows[32], uint32_t x)
+{
+    uint32_t y = 0;
+    for (int r = 0; r < 32; ++r) {
+        uint32_t t = rows[r] & x, par = 0;
+        while (t) { par ^= 1u; t &= t - 1u; }
+        y |= par << (31 - r);
+    }
+    return y;
+}
+
 /* ------------------------------------------------------------------ */
 /* Sequence object: randomization of every (m, j) for one call.        */
 /* ------------------------------------------------------------------ */
-enum { ORC_HALTON_RS = 0, ORC_RASRAP = 1, ORC_SOBOL_DS = 2, ORC_PHILOX = 3 };
+enum { ORC_HALTON_RS = 0, ORC_RASRAP = 1, ORC_SOBOL_DS = 2, ORC_PHILOX = 3, ORC_SOBOL_LMS = 4 };
 
 typedef struct {
     int seq, s, M;
@@ -256,19 +286,20 @@ typedef struct {
     uint16_t *sigma;    /* [M][sig_len] */
     uint32_t *V;        /* [s][32] */
     uint32_t *shift;    /* [M][s] */
+    uint32_t *lms;      /* [M][s][32] scrambling rows (ORC_SOBOL_LMS) */
 } orc_seq;
 
 void orc_seq_destroy(orc_seq *q)
 {
     if (!q) return;
     free(q->p); free(q->K); free(q->D); free(q->n0); free(q->sig_off);
-    free(q->sigma); free(q->V); free(q->shift); free(q);
+    free(q->sigma); free(q->V); free(q->shift); free(q->lms); free(q);
 }
 
 orc_seq *orc_seq_create(int seq, int s, int M, uint64_t seed, uint32_t inst,
                         const int64_t *poly, const int64_t *vinit, int maxdeg)
 {
-    if (s < 1 || M < 1 || seq < 0 || seq > 3) return NULL;
+    if (s < 1 || M < 1 || seq < 0 || seq > 4) return NULL;
     orc_seq *q = (orc_seq *)calloc(1, sizeof(orc_seq));
     q->seq = seq; q->s = s; q->M = M; q->seed = seed; q->inst = inst;
     q->D = (uint64_t *)calloc((size_t)s, sizeof(uint64_t));
@@ -292,7 +323,7 @@ orc_seq *orc_seq_create(int seq, int s, int M, uint64_t seed, uint32_t inst,
                 orc_halton_perm(seed, inst, m, j, q->p[j], seq == ORC_HALTON_RS,
                                 q->sigma + (size_t)m * q->sig_len + q->sig_off[j]);
             }
-    } else if (seq == ORC_SOBOL_DS) {
+    } else if (seq == ORC_SOBOL_DS || seq == ORC_SOBOL_LMS) {
         if (!poly || !vinit) { orc_seq_destroy(q); return NULL; }
         q->V = (uint32_t *)calloc((size_t)s * 32, sizeof(uint32_t));
         if (orc_sobol_directions(s, poly, vinit, maxdeg, q->V) != 0) { orc_seq_destroy(q); return NULL; }
@@ -300,6 +331,11 @@ orc_seq *orc_seq_create(int seq, int s, int M, uint64_t seed, uint32_t inst,
         for (int m = 0; m < M; ++m)
             for (int j = 0; j < s; ++j)
                 q->shift[(size_t)m * s + j] = orc_sobol_shift(seed, inst, m, j);
+        if (seq == ORC_SOBOL_LMS) {
+            q->lms = (uint32_t *)calloc((size_t)M * s * 32, sizeof(uint32_t));
+            for (int m = 0; m < M; ++m)
+                for (int j = 0; j < s; ++j) orc_sobol_lms_rows(seed, inst, m, j, q->lms + ((size_t)m * s + j) * 32);
+        }
         for (int j = 0; j < s; ++j) q->D[j] = (uint64_t)1 << 32;
     } else {
         for (int j = 0; j < s; ++j) q->D[j] = (uint64_t)1 << 32;
@@ -322,6 +358,10 @@ uint64_t orc_coord_raw(const orc_seq *q, int m, int j, uint64_t n, uint64_t *D)
     }
     case ORC_SOBOL_DS:
         return (uint64_t)(orc_sobol_binary(q->V + (size_t)j * 32, n) ^ q->shift[(size_t)m * q->s + j]);
+    case ORC_SOBOL_LMS:
+        return (uint64_t)(orc_sobol_lms_apply(q->lms + ((size_t)m * q->s + j) * 32,
+                                              orc_sobol_binary(q->V + (size_t)j * 32, n)) ^
+                          q->shift[(size_t)m * q->s + j]);
     default:
         return (uint64_t)orc_philox_path_word(q->seed, q->inst, m, j, n);
     }

@@ -282,6 +282,75 @@ def test_digital_shift_keeps_stratification():
                 assert sorted(blk.tolist()) == list(range(1 << k))
 
 
+def _lms_rows(seed, inst, m, j):
+    import ctypes as C
+    rows = np.zeros(32, dtype=np.uint32)
+    O.lib().orc_sobol_lms_rows(seed, inst, m, j, rows.ctypes.data_as(C.POINTER(C.c_uint32)))
+    return rows
+
+
+def test_lms_matrices_are_random_unit_lower_triangular():
+    # Sec. 3.2 (Matousek): nonsingular lower-triangular scrambling matrices
+    ones = np.zeros((32, 32))
+    for m in range(10):
+        for j in range(20):
+            rows = _lms_rows(7, 0, m, j)
+            for r in range(32):
+                row = int(rows[r])
+                assert (row >> (31 - r)) & 1 == 1                 # unit diagonal
+                assert row & ((1 << (31 - r)) - 1) == 0           # nothing right of it
+                for l in range(r):
+                    ones[r, l] += (row >> (31 - l)) & 1
+    frac = ones[np.tril_indices(32, -1)] / 200.0
+    assert 0.35 < frac.mean() < 0.65 and frac.min() > 0.3 and frac.max() < 0.7
+
+
+def test_lms_equals_explicit_gf2_matrix_product():
+    # y = L (C n) + e over GF(2), written as plain 0/1 matrix algebra: C's column k holds
+    # the digits of direction number v_k (digit l = 2^-(l+1)), n's digit k is bit k.
+    poly, vinit = inputs.joe_kuo_table()
+    s, M, seed = 12, 3, 21
+    q = O.Sequence(O.SOBOL_LMS, s, M, seed, joe_kuo=(poly, vinit))
+    V = O.sobol_directions(s, poly, vinit)
+    digits = lambda x: np.array([(int(x) >> (31 - l)) & 1 for l in range(32)], dtype=np.int64)
+    rng = np.random.default_rng(3)
+    for m in range(M):
+        for j in range(s):
+            rows = _lms_rows(seed, 0, m, j)
+            Lm = np.array([digits(r) for r in rows])                    # row r = output digit r
+            Cm = np.array([digits(v) for v in V[j]]).T                  # column k = v_k
+            e = digits(O.sobol_shift(seed, 0, m, j))
+            for n in [0, 1, 2, 3, 1023, 65535] + rng.integers(0, 1 << 31, 6).tolist():
+                nb = np.array([(n >> k) & 1 for k in range(32)], dtype=np.int64)
+                y = (Lm @ ((Cm @ nb) % 2) + e) % 2
+                want = sum(int(y[l]) << (31 - l) for l in range(32))
+                assert q.raw(m, j, n)[0] == want
+
+
+def test_lms_keeps_stratification_and_the_two_dimensional_net():
+    q = O.Sequence(O.SOBOL_LMS, 40, 2, seed=9, joe_kuo=inputs.joe_kuo_table())
+    raw = q.points(1024, transform=O.RAW)
+    for m in range(2):
+        for j in range(40):
+            for k in (3, 6, 10):
+                assert sorted((raw[m, j, :1 << k] >> (32 - k)).tolist()) == list(range(1 << k))
+        # dimensions 0 and 1 of Sobol' form a (0, m, 2)-net in base 2, and a nonsingular
+        # lower-triangular scrambling plus a shift keeps it: every elementary box of volume
+        # 2^-8 holds exactly one of the first 2^8 points
+        x, y = raw[m, 0, :256], raw[m, 1, :256]
+        for k1 in range(9):
+            cells = (x >> (32 - k1) if k1 else 0 * x) * (1 << (8 - k1)) + (y >> (24 + k1) if k1 < 8 else 0 * y)
+            assert len(set(cells.tolist())) == 256
+
+
+def test_lms_differs_from_the_shift_alone():
+    jk = inputs.joe_kuo_table()
+    a = O.Sequence(O.SOBOL_LMS, 8, 1, seed=4, joe_kuo=jk).points(64, transform=O.RAW)
+    b = O.Sequence(O.SOBOL_DS, 8, 1, seed=4, joe_kuo=jk).points(64, transform=O.RAW)
+    assert np.all(a[0, :, 0] == b[0, :, 0])          # point 0: x = 0, so L x = 0, only the shift
+    assert np.mean(a != b) > 0.8
+
+
 # ------------------------------------------------------------------ inverse normal
 def test_ndtri_matches_scipy():
     special = pytest.importorskip("scipy.special")
