@@ -13,6 +13,9 @@
  *                   Algorithm 3; a new start and new permutations for every replication)
  *   RQMC_SOBOL_DS   Sobol' in binary counter order (Sec. 3.2), digitally shifted per replication
  *   RQMC_PHILOX     the counter-based pseudorandom stream Philox4x32-10 (Sec. 2)
+ *   RQMC_SOBOL_LMS  Sobol' with Matousek's random linear scrambling (Sec. 3.2): per replication
+ *                   and dimension a random unit lower-triangular binary matrix acts on the
+ *                   binary digits of every coordinate, followed by a digital shift
  * Randomizations are drawn from Philox4x32-10 keyed by `seed`, so a call is
  * reproducible bit for bit from (seq, s, M, seed).
  *
@@ -63,7 +66,13 @@ typedef enum {
     RQMC_ENOTABLE = 6       /* Sobol' requested before rqmc_set_sobol_table covered s dims */
 } rqmc_status;
 
-typedef enum { RQMC_HALTON_RS = 0, RQMC_RASRAP = 1, RQMC_SOBOL_DS = 2, RQMC_PHILOX = 3 } rqmc_sequence;
+typedef enum {
+    RQMC_HALTON_RS = 0,
+    RQMC_RASRAP = 1,
+    RQMC_SOBOL_DS = 2,
+    RQMC_PHILOX = 3,
+    RQMC_SOBOL_LMS = 4
+} rqmc_sequence;
 typedef enum { RQMC_FP64 = 0, RQMC_FP32 = 1 } rqmc_precision;
 typedef enum { RQMC_UNIFORM = 0, RQMC_NORMAL = 1, RQMC_RAW = 2 } rqmc_transform;
 typedef enum { RQMC_LOG_EULER = 0 } rqmc_lmm_scheme;

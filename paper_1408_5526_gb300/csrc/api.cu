@@ -51,7 +51,7 @@ static rqmc_status common_checks(int s, int64_t N, int64_t offset, int M, int se
     if (N < 1 || N > (int64_t(1) << 31)) { set_error("N must be in 1..2^31"); return RQMC_EINVAL; }
     if (offset < 0) { set_error("offset must be >= 0"); return RQMC_EINVAL; }
     if (M < 1 || M > 65535) { set_error("M must be in 1..65535"); return RQMC_EINVAL; }
-    if (seq < 0 || seq > 3) { set_error("unknown sequence"); return RQMC_EINVAL; }
+    if (seq < 0 || seq > 4) { set_error("unknown sequence"); return RQMC_EINVAL; }
     if (prec != RQMC_FP64 && prec != RQMC_FP32) { set_error("unknown precision"); return RQMC_EINVAL; }
     return RQMC_OK;
 }

@@ -297,7 +297,7 @@ struct rqmc_plan_s : public Plan {};
 
 extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *inst, int n, int M, rqmc_sequence seq, uint64_t seed,
                                        rqmc_precision prec, rqmc_plan **plan) {
-    if (!inst || !plan || n < 1 || n > (1 << 20) || M < 1 || M > 65535 || seq < 0 || seq > 3) {
+    if (!inst || !plan || n < 1 || n > (1 << 20) || M < 1 || M > 65535 || seq < 0 || seq > 4) {
         set_error("batch: instruments, n in 1..2^20 and M in 1..65535 are required");
         return RQMC_EINVAL;
     }

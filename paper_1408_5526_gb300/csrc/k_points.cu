@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(256) points_kernel(const GenParams g, uint32_t
                 uint32_t n[kPtItems], x[kPtItems];
 #pragma unroll
                 for (int it = 0; it < kPtItems; ++it) n[it] = (uint32_t)(g.offset + ii[it]);
-                sobol_lockstep<kPtItems>(g.sobV + 32 * j, __ldg(g.sobShift + row), n, g.sob_bits, x);
+                sobol_lockstep<kPtItems>(g.sobV + (size_t)m * g.sobV_mstride + 32 * j, __ldg(g.sobShift + row), n,
+                                         g.sob_bits, x);
                 if constexpr (TR == RQMC_NORMAL && sizeof(T) == 4) {
                     Unif32 u[kPtItems];
                     float z[kPtItems];

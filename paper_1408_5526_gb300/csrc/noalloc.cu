@@ -94,7 +94,7 @@ extern "C" rqmc_status rqmc_price_caplets_noalloc(const rqmc_lmm_params *p, cons
     }
     if (p->n_fwd < 1 || p->n_fwd > kMaxFwd || p->n_factors != 1 || p->scheme != RQMC_LOG_EULER ||
         !(p->delta > 0.0) || !std::isfinite(p->delta) || n_strikes < 1 || n_strikes > kMaxStrikes ||
-        N < 1 || N > (int64_t(1) << 31) || M < 1 || M > 65535 || seq < 0 || seq > 3 ||
+        N < 1 || N > (int64_t(1) << 31) || M < 1 || M > 65535 || seq < 0 || seq > 4 ||
         (prec != RQMC_FP32 && prec != RQMC_FP64)) {
         set_error("rqmc_price_caplets_noalloc: argument out of range (one-factor log-Euler, 1..160 forwards, "
                   "1..8 strikes, N in 1..2^31, M in 1..65535)");

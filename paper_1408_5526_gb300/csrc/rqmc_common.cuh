@@ -71,10 +71,12 @@ __host__ __device__ __forceinline__ U32x4 philox4x32_10(uint32_t c0, uint32_t c1
 }
 
 // Counter tags (low byte of counter word 3; the instrument index sits above it).
-enum : uint32_t { kTagPath = 0, kTagStart = 1, kTagPerm = 2, kTagShift = 3 };
+enum : uint32_t { kTagPath = 0, kTagStart = 1, kTagPerm = 2, kTagShift = 3, kTagScramble = 4 };
 
 // ------------------------------------------------------------------ sequence descriptors
-enum Seq : int { kHaltonRS = 0, kRasrap = 1, kSobolDS = 2, kPhilox = 3 };
+// kSobolLMS is a plan-level sequence only: its kernels run the kSobolDS code on
+// per-replication (scrambled) direction numbers.
+enum Seq : int { kHaltonRS = 0, kRasrap = 1, kSobolDS = 2, kPhilox = 3, kSobolLMS = 4 };
 
 // Per (replication m, dimension j) description of the random-start permuted van der
 // Corput points phi_p^sigma(n0 + offset + i), i < N, split at digit L:
@@ -106,7 +108,8 @@ struct GenParams {
     const HaltonDim *hdim;   // [M][s]
     const uint16_t *sigma;   // [M][sig_len]
     unsigned long long sig_len;
-    const uint32_t *sobV;    // [s][32]
+    const uint32_t *sobV;    // [s][32], or [M][s][32] when scrambled per replication
+    unsigned long long sobV_mstride;   // 0, or 32 s for per-replication tables
     const uint32_t *sobShift;// [M][s]
     int sob_bits;            // bits of offset + N - 1
     int stage_sig;           // 1: a replication's permutations are staged in shared memory
@@ -168,7 +171,8 @@ __device__ __forceinline__ void stage_tables(const GenParams &g, int m, unsigned
     } else if (g.seq == kSobolDS) {
         uint32_t *V = reinterpret_cast<uint32_t *>(sm);
         uint32_t *sh = reinterpret_cast<uint32_t *>(sm + align16(4ull * 32 * g.s));
-        for (int k = threadIdx.x; k < 32 * g.s; k += blockDim.x) V[k] = g.sobV[k];
+        const uint32_t *Vm = g.sobV + (size_t)m * g.sobV_mstride;
+        for (int k = threadIdx.x; k < 32 * g.s; k += blockDim.x) V[k] = Vm[k];
         for (int k = threadIdx.x; k < g.s; k += blockDim.x) sh[k] = g.sobShift[(size_t)m * g.s + k];
         v.V = V;
         v.shift = sh;
@@ -310,10 +314,10 @@ struct PathGen {
 };
 
 // Runtime sequence -> compile-time generator (HALTON_RS and RASRAP share one code path).
-#define RQMC_SEQ_DISPATCH(seq, F)              \
-    ((seq) == kPhilox    ? F(kPhilox)          \
-     : (seq) == kSobolDS ? F(kSobolDS)         \
-                         : F(kRasrap))
+#define RQMC_SEQ_DISPATCH(seq, F)                                \
+    ((seq) == kPhilox                            ? F(kPhilox)    \
+     : ((seq) == kSobolDS || (seq) == kSobolLMS) ? F(kSobolDS)   \
+                                                 : F(kRasrap))
 
 // ------------------------------------------------------------------ inverse normal CDF
 // erfinv(y)/y as a polynomial in w = -ln(4q(1-q)) (three branches, coefficients

@@ -177,7 +177,7 @@ struct Carve {
 
 // ---- setup (setup.cu)
 struct GenLayout {
-    size_t hdim_off = 0, sigma_off = 0, base_off = 0, sobV_off = 0, shift_off = 0;
+    size_t hdim_off = 0, sigma_off = 0, base_off = 0, sobV_off = 0, shift_off = 0, scr_off = 0;
     unsigned long long sig_len = 0;
     std::vector<BaseConst> bases;
 };

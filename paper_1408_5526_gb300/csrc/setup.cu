@@ -170,6 +170,40 @@ __global__ void setup_shift_kernel(int s, int M, uint32_t key0, uint32_t key1, u
     shift[idx] = philox4x32_10((uint32_t)j, 0u, (uint32_t)m, kTagShift | (inst << 8), key0, key1).x;
 }
 
+// Matousek's random linear scrambling (Sec. 3.2): per (m, j) a unit lower-triangular binary
+// matrix L over the coordinate's binary digits (most significant first).  Row r (output
+// digit r) is a 32-bit mask over the input digits (digit l = bit 31 - l) with the diagonal
+// set and, left of it, the top r bits of Philox word r - 1 of counters (j, (r-1)/4, m,
+// tag 4).  The map is linear, L(XOR_k n_k v_k) = XOR_k n_k (L v_k), so the replication's
+// direction numbers are scrambled once here and the kernels run the plain Sobol' code.
+__global__ void setup_scramble_kernel(int s, int M, uint32_t key0, uint32_t key1, uint32_t inst,
+                                      const uint32_t *__restrict__ V, uint32_t *__restrict__ out) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= M * s) return;
+    const int m = idx / s, j = idx % s;
+    uint32_t rows[32];
+    rows[0] = 0x80000000u;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const U32x4 w = philox4x32_10((uint32_t)j, (uint32_t)b, (uint32_t)m, kTagScramble | (inst << 8), key0, key1);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = 4 * b + q + 1;   // row r uses word r - 1
+            if (r < 32) rows[r] = ((ws[q] >> (32 - r)) << (32 - r)) | (0x80000000u >> r);
+        }
+    }
+    const uint32_t *Vj = V + 32 * j;
+    uint32_t *o = out + (size_t)idx * 32;
+    for (int k = 0; k < 32; ++k) {
+        const uint32_t v = Vj[k];
+        uint32_t y = 0;
+#pragma unroll
+        for (int r = 0; r < 32; ++r) y |= (uint32_t)(__popc(rows[r] & v) & 1) << (31 - r);
+        o[k] = y;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 static int halton_K(uint32_t p) {
     unsigned long long pw = p;
@@ -218,7 +252,7 @@ rqmc_status generator_layout(Plan &pl, Carve &cv, GenLayout &gl) {
         gl.hdim_off = cv.take(sizeof(HaltonDim) * (size_t)M * s);
         gl.sigma_off = cv.take(sizeof(uint16_t) * (size_t)M * off);
         gl.base_off = cv.take(sizeof(BaseConst) * (size_t)s);
-    } else if (pl.seq == kSobolDS) {
+    } else if (pl.seq == kSobolDS || pl.seq == kSobolLMS) {
         if (!sobol_table_ready(s)) {
             set_error("Sobol': direction table covers fewer than s dimensions (call rqmc_set_sobol_table)");
             return RQMC_ENOTABLE;
@@ -229,6 +263,7 @@ rqmc_status generator_layout(Plan &pl, Carve &cv, GenLayout &gl) {
         }
         gl.sobV_off = cv.take(sizeof(uint32_t) * 32 * (size_t)s);
         gl.shift_off = cv.take(sizeof(uint32_t) * (size_t)M * s);
+        if (pl.seq == kSobolLMS) gl.scr_off = cv.take(sizeof(uint32_t) * 32 * (size_t)M * s);
     } else {
         if (pl.offset + pl.N > (1ull << 48)) {
             set_error("Philox: offset + N must not exceed 2^48");
@@ -241,7 +276,7 @@ rqmc_status generator_layout(Plan &pl, Carve &cv, GenLayout &gl) {
 rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint32_t *d_status, cudaStream_t st) {
     const int s = pl.s, M = pl.M;
     GenParams &g = pl.gen;
-    g.seq = pl.seq;
+    g.seq = pl.seq == kSobolLMS ? kSobolDS : pl.seq;   // kernels run scrambled tables as plain ones
     g.s = s;
     g.M = M;
     g.key0 = (uint32_t)pl.seed;
@@ -260,7 +295,7 @@ rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint
         setup_halton_kernel<<<nblk, nthr, 0, st>>>(db, s, M, g.key0, g.key1, g.inst, pl.offset, pl.N,
                                                    pl.seq == kHaltonRS ? 1 : 0, const_cast<HaltonDim *>(g.hdim),
                                                    const_cast<uint16_t *>(g.sigma), gl.sig_len, d_status);
-    } else if (pl.seq == kSobolDS) {
+    } else if (pl.seq == kSobolDS || pl.seq == kSobolLMS) {
         uint32_t *V = reinterpret_cast<uint32_t *>(d + gl.sobV_off);
         uint32_t *sh = reinterpret_cast<uint32_t *>(d + gl.shift_off);
         {
@@ -272,7 +307,14 @@ rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint
         }
         setup_shift_kernel<<<nblk, nthr, 0, st>>>(s, M, g.key0, g.key1, g.inst, sh);
         g.sobV = V;
+        g.sobV_mstride = 0;
         g.sobShift = sh;
+        if (pl.seq == kSobolLMS) {
+            uint32_t *scr = reinterpret_cast<uint32_t *>(d + gl.scr_off);
+            setup_scramble_kernel<<<nblk, nthr, 0, st>>>(s, M, g.key0, g.key1, g.inst, V, scr);
+            g.sobV = scr;
+            g.sobV_mstride = 32ull * s;
+        }
         unsigned long long last = pl.offset + pl.N - 1;
         int bits = 1;
         while (bits < 32 && (last >> bits) != 0) ++bits;

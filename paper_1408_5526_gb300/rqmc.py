@@ -19,10 +19,10 @@ from . import inputs
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "librqmc.so")
 
-HALTON_RS, RASRAP, SOBOL_DS, PHILOX = 0, 1, 2, 3
+HALTON_RS, RASRAP, SOBOL_DS, PHILOX, SOBOL_LMS = 0, 1, 2, 3, 4
 FP64, FP32 = 0, 1
 UNIFORM, NORMAL, RAW = 0, 1, 2
-_SEQ = {"halton_rs": HALTON_RS, "rasrap": RASRAP, "sobol_ds": SOBOL_DS, "philox": PHILOX}
+_SEQ = {"halton_rs": HALTON_RS, "rasrap": RASRAP, "sobol_ds": SOBOL_DS, "philox": PHILOX, "sobol_lms": SOBOL_LMS}
 _PREC = {"fp64": FP64, "fp32": FP32}
 _TR = {"uniform": UNIFORM, "normal": NORMAL, "raw": RAW}
 STATUS = {0: "RQMC_OK", 1: "RQMC_EINVAL", 2: "RQMC_ENOMEM", 3: "RQMC_ECUDA", 4: "RQMC_ETIMEOUT",

@@ -19,7 +19,8 @@ def R():
     return rqmc
 
 
-@pytest.mark.parametrize("seq,d,nf", [(O.SOBOL_DS, 2, 10), (O.RASRAP, 2, 13), (O.PHILOX, 1, 9), (O.SOBOL_DS, 1, 45)])
+@pytest.mark.parametrize("seq,d,nf", [(O.SOBOL_DS, 2, 10), (O.RASRAP, 2, 13), (O.PHILOX, 1, 9), (O.SOBOL_DS, 1, 45),
+                                      (O.SOBOL_LMS, 2, 17)])
 def test_adjoint_matches_oracle(R, seq, d, nf):
     lm = inputs.lmm_two_factor(n_fwd=nf, seed=3) if d == 2 else inputs.lmm_flat(nf, vol=0.2)
     lm["L0"] = np.linspace(0.045, 0.055, nf + 1)

@@ -43,7 +43,7 @@ def _oracle(seq, M, seed, insts=INSTS):
     return out
 
 
-@pytest.mark.parametrize("seq", [O.SOBOL_DS, O.RASRAP, O.PHILOX])
+@pytest.mark.parametrize("seq", [O.SOBOL_DS, O.RASRAP, O.PHILOX, O.SOBOL_LMS])
 def test_batch_matches_oracle_per_instrument(R, seq):
     M, seed = 2, 11
     got = R.price_batch(INSTS, M, seq, seed)

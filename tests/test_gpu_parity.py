@@ -29,6 +29,7 @@ def _to_np(t):
 
 # ------------------------------------------------------------------ point stream
 @pytest.mark.parametrize("seq,s", [(O.HALTON_RS, 8), (O.RASRAP, 8), (O.RASRAP, 360), (O.SOBOL_DS, 40),
+                                   (O.SOBOL_LMS, 40), (O.SOBOL_LMS, 360),
                                    (O.SOBOL_DS, 360), (O.PHILOX, 10)])
 @pytest.mark.parametrize("offset", [0, 12345])
 def test_points_raw_bit_exact(R, seq, s, offset):
@@ -39,7 +40,7 @@ def test_points_raw_bit_exact(R, seq, s, offset):
     assert np.array_equal(gpu, ora)
 
 
-@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX])
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
 @pytest.mark.parametrize("prec,transform", [("fp32", "normal"), ("fp64", "uniform"), ("fp32", "raw")])
 def test_points_plan_matches_one_shot(R, seq, prec, transform):
     """The point-stream plan (tables built once) writes exactly what rqmc_points writes,
@@ -54,7 +55,7 @@ def test_points_plan_matches_one_shot(R, seq, prec, transform):
     assert a.shape == ref.shape and np.array_equal(a, ref) and np.array_equal(b, ref)
 
 
-@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX])
+@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
 def test_points_fp64_uniform_and_normal(R, seq):
     N, M, s = 2500, 2, 16
     q = O.Sequence(seq, s, M, 11, joe_kuo=JK)
@@ -65,7 +66,7 @@ def test_points_fp64_uniform_and_normal(R, seq):
     np.testing.assert_allclose(z, zo, rtol=0, atol=2e-14 * np.maximum(1, np.abs(zo)).max())
 
 
-@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX])
+@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
 def test_points_fp32_uniform_and_normal(R, seq):
     N, M, s = 2500, 2, 40
     q = O.Sequence(seq, s, M, 13, joe_kuo=JK)
@@ -88,7 +89,7 @@ def test_points_halton_tail_normals_fp32(R):
 
 
 # ------------------------------------------------------------------ product integrand
-@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX])
+@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
 def test_product_theta(R, seq):
     cfg = inputs.CONFIGS["product_s8"]
     s, N, M = cfg["s"], cfg["N"], cfg["M"]
@@ -109,7 +110,7 @@ def _caplet_tol(theta_o, nK):
     return 1e-4 * scale.reshape(theta_o.shape)
 
 
-@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS])
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS, O.SOBOL_LMS])
 def test_caplets_small(R, seq):
     lm = inputs.lmm_flat(40)
     K = inputs.LMM_STRIKES
@@ -121,7 +122,7 @@ def test_caplets_small(R, seq):
     assert np.all(np.abs(th32 - th_o) <= _caplet_tol(th_o, len(K)))
 
 
-@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX])
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
 def test_caplets_treasury_curve(R, seq):
     """Sec. 5's Treasury-curve study inputs (non-flat curve, delta = 0.5, sigma = 4 %,
     K = 1 %) against the oracle in FP64 and FP32."""
@@ -149,7 +150,7 @@ def test_caplets_bucket_edges(R, nf):
     assert np.all(np.abs(th32 - th_o) <= 1e-4 * np.abs(th_o) + 1e-9)
 
 
-@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX])
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
 def test_caplets_full_size_sampled(R, seq):
     """The 40-forward, N = 65536, M = 64 workload as the bench runs it; the oracle
     recomputes two replications at full N."""
@@ -165,7 +166,7 @@ def test_caplets_full_size_sampled(R, seq):
 
 
 # ------------------------------------------------------------------ MBS
-@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS])
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS, O.SOBOL_LMS])
 def test_mbs_small(R, seq):
     mb = inputs.mbs_paper(360)
     N, M = 1500, 2
