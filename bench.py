@@ -323,7 +323,7 @@ def other_workloads(args, dev, seed):
     st = inputs.TREASURY_STUDY
     lmt = inputs.lmm_treasury(st["T"], st["delta"], st["vol"])
     study = {}
-    for s_ in SEQS:
+    for s_ in SEQS + ("sobol_lms",):
         rows = []
         for e in range(10, 21, 2):
             pt = rqmc.Plan.caplets(lmt, [st["K"]], 1 << e, st["M"], s_, seed, prec="fp32")
@@ -337,6 +337,14 @@ def other_workloads(args, dev, seed):
         ly = np.log([r["std"] for r in rows])
         study[s_] = {"rate": float(np.polyfit(lx, ly, 1)[0]), "by_N": rows}
     out["lmm_treasury_study_T5_M100_fp32"] = study
+    # Matousek-scrambled Sobol' on the headline caplet workload (same kernel, scrambled tables)
+    pl_ = rqmc.Plan.caplets(inputs.lmm_flat(N_FWD), inputs.LMM_STRIKES, N_PATHS, M_REPL, "sobol_lms", seed,
+                            prec="fp32")
+    o_ = torch.empty(pl_.output_size(), dtype=torch.float64, device=dev)
+    ms = _time_plan(lambda: pl_.execute(o_), 3, flush)
+    pl_.close()
+    out["lmm_caplets_40_N65536_M64_fp32_sobol_lms"] = {"ms": ms,
+                                                       "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3)}
     # point stream: s = 360, N = 65536, M = 64 FP32 normals, written to HBM
     buf = torch.empty((M_REPL, 360, N_PATHS), dtype=torch.float32, device=dev)
     res = {}
