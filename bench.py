@@ -217,6 +217,7 @@ def run_ours(args, rank, world):
                            "(probe: ex2 29.8, rcp 15.1, lg2 15.4 per SM per clock)"}
     extra = other_workloads(args, dev, seed) if (rank == 0 and not args.no_extra) else None
     cpu = cpu_baseline(args) if (rank == 0 and not args.no_cpu) else None
+    cpu_gen = cpu_generators() if (rank == 0 and not args.no_cpu) else None
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -241,6 +242,7 @@ def run_ours(args, rank, world):
             "gpu_launches": args.steps * sum(p.launches() for p in plans),
             "clocks": clocks,
             "workloads": extra,
+            "cpu_generators_table1": cpu_gen,
         }
         print(json.dumps(line), flush=True)
     for p in plans:
@@ -377,6 +379,31 @@ def cpu_baseline(args, seconds_hint=True):
     dt = time.perf_counter() - t0
     return {"value": cores * N_PATHS * N_FWD / dt, "unit": "path-steps/s", "cores": cores, "kind": "oracle",
             "sample": f"rasrap, {cores} replications x N={N_PATHS} x 40 steps ({dt:.1f} s)"}
+
+
+def cpu_generators():
+    """Table 1 style CPU generator throughput on this host, for context beside the GPU point
+    stream: the recursive generators (Algorithm 2 for Rasrap, Gray-code order for Sobol')
+    and the counter-based forms (Algorithm 3, binary-order Sobol', Philox) of the oracle,
+    raw integer states of s = 40 dimensions, M = 8, N = 65536, one thread and all threads
+    (capped at 16)."""
+    import oracle as O
+    from paper_1408_5526_gb300 import inputs
+    jk = inputs.joe_kuo_table()
+    cores = min(O.max_threads(), 16)
+    out = {"cores": cores, "unit": "GNumbers/s", "sample": "s=40, M=8, N=65536 raw states"}
+    for name, seq in (("rasrap", O.RASRAP), ("sobol_ds", O.SOBOL_DS), ("philox", O.PHILOX)):
+        q = O.Sequence(seq, 40, 8, SEED, joe_kuo=jk if seq == O.SOBOL_DS else None)
+        row = {}
+        for th in (1, cores):
+            t0 = time.perf_counter()
+            a = q.stream(0, 65536, threads=th)
+            row[f"recursive_{th}t"] = a.size / (time.perf_counter() - t0) / 1e9
+        t0 = time.perf_counter()
+        b = q.points(65536, transform=O.RAW, threads=cores)
+        row[f"counter_based_{cores}t"] = b.size / (time.perf_counter() - t0) / 1e9
+        out[name] = row
+    return out
 
 
 def run_reference(args, rank, world):

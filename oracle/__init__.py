@@ -78,6 +78,10 @@ def lib():
         L.orc_sobol_lms_rows.restype = None
         L.orc_sobol_lms_apply.argtypes = [u32p, C.c_uint32]
         L.orc_sobol_lms_apply.restype = C.c_uint32
+        L.orc_stream_raw.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_uint64, C.c_uint64, u64p]
+        L.orc_stream_raw.restype = C.c_int
+        L.orc_stream_rows.argtypes = [C.c_void_p, C.c_uint64, C.c_uint64, C.c_int, u64p]
+        L.orc_stream_rows.restype = C.c_int
         L.orc_sobol_shift.restype = C.c_uint32
         L.orc_philox_path_word.argtypes = [C.c_uint64, C.c_uint32, C.c_int, C.c_int, C.c_uint64]
         L.orc_philox_path_word.restype = C.c_uint32
@@ -204,6 +208,15 @@ class Sequence:
         if getattr(self, "h", None) and _lib is not None:
             _lib.orc_seq_destroy(self.h)
             self.h = None
+
+    def stream(self, n_start: int, count: int, threads: int = 0) -> np.ndarray:
+        """Raw states [M, s, count] from the recursive CPU generators of Table 1 (Algorithm 2
+        for Halton/Rasrap, Gray-code order for Sobol'; Philox is counter-based)."""
+        out = np.zeros((self.M, self.s, count), dtype=np.uint64)
+        rc = lib().orc_stream_rows(self.h, n_start, count, threads or max_threads(), _p(out, C.c_uint64))
+        if rc != 0:
+            raise ValueError("point range outside the representable digits")
+        return out
 
     def raw(self, m: int, j: int, n: int):
         D = C.c_uint64(0)

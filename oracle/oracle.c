@@ -368,6 +368,86 @@ uint64_t orc_coord_raw(const orc_seq *q, int m, int j, uint64_t n, uint64_t *D)
 }
 
 /* ------------------------------------------------------------------ */
+/* Recursive CPU generators of Table 1 (Sec. 4), for the CPU timing      */
+/* baselines: count consecutive raw states of row (m, j) from point      */
+/* n_start on.                                                           */
+/*  - Halton / Rasrap: Algorithm 2, an odometer on the digits a_0..a_K   */
+/*    of n0 + n with the suffix sums S_k = sum_{i >= k} of the permuted  */
+/*    digit terms cached, so one step touches only the digits the carry  */
+/*    changed (same numerators as the counter-based form, reading c2).   */
+/*  - Sobol' (shifted or scrambled): Antonov-Saleev Gray-code order:     */
+/*    element c is the point of index g(n_start + c), g(n) = n ^ (n>>1); */
+/*    the next one is one XOR with the direction number of the lowest    */
+/*    zero bit of n (scrambling applied to the direction numbers, which  */
+/*    is the same map by linearity).                                     */
+/*  - Philox: counter-based.                                             */
+/* ------------------------------------------------------------------ */
+int orc_stream_raw(const orc_seq *q, int m, int j, uint64_t n_start, uint64_t count, uint64_t *out)
+{
+    if (q->seq == ORC_HALTON_RS || q->seq == ORC_RASRAP) {
+        const uint32_t p = q->p[j];
+        const int K = q->K[j];
+        const uint16_t *sg = q->sigma + (size_t)m * q->sig_len + q->sig_off[j];
+        uint64_t idx = q->n0[(size_t)m * q->s + j] + n_start;
+        if (idx + count > q->D[j]) return -1;
+        uint64_t a[64], w[64], S[65];
+        for (int k = 0; k <= K; ++k) {
+            a[k] = idx % p;
+            idx /= p;
+            w[k] = orc_ipow(p, K - k);
+        }
+#define ORC_TERM(k, d) ((k) < K ? (uint64_t)sg[d] * w[k] : ((d) ? (uint64_t)sg[d] : 0u))
+        S[K + 1] = 0;
+        for (int k = K; k >= 0; --k) S[k] = S[k + 1] + ORC_TERM(k, a[k]);
+        for (uint64_t c = 0; c < count; ++c) {
+            out[c] = S[0];
+            int k = 0;
+            while (k <= K && a[k] == p - 1) { a[k] = 0; ++k; }
+            if (k > K) { if (c + 1 < count) return -1; break; }
+            a[k] += 1;
+            S[k] = S[k + 1] + ORC_TERM(k, a[k]);
+            for (int i = k - 1; i >= 0; --i) S[i] = S[i + 1] + ORC_TERM(i, 0);
+        }
+#undef ORC_TERM
+        return 0;
+    }
+    if (q->seq == ORC_SOBOL_DS || q->seq == ORC_SOBOL_LMS) {
+        uint32_t V[32];
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t v = q->V[(size_t)j * 32 + k];
+            V[k] = q->seq == ORC_SOBOL_LMS ? orc_sobol_lms_apply(q->lms + ((size_t)m * q->s + j) * 32, v) : v;
+        }
+        const uint32_t e = q->shift[(size_t)m * q->s + j];
+        uint64_t n = n_start;
+        uint32_t x = 0;
+        const uint64_t g = n ^ (n >> 1);
+        for (int k = 0; k < 32; ++k)
+            if ((g >> k) & 1u) x ^= V[k];
+        for (uint64_t c = 0; c < count; ++c, ++n) {
+            out[c] = (uint64_t)(x ^ e);
+            int z = 0;
+            while ((n >> z) & 1u) ++z;   /* lowest zero bit of n: g(n+1) = g(n) ^ 2^z */
+            if (z < 32) x ^= V[z];
+        }
+        return 0;
+    }
+    for (uint64_t c = 0; c < count; ++c)
+        out[c] = (uint64_t)orc_philox_path_word(q->seed, q->inst, m, j, n_start + c);
+    return 0;
+}
+
+/* All rows [M][s][count] of the stream, OpenMP over rows. */
+int orc_stream_rows(const orc_seq *q, uint64_t n_start, uint64_t count, int threads, uint64_t *out)
+{
+    int bad = 0;
+    const int rows = q->M * q->s;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(threads) reduction(| : bad)
+    for (int r = 0; r < rows; ++r)
+        bad |= orc_stream_raw(q, r / q->s, r % q->s, n_start, count, out + (size_t)r * count) != 0;
+    return bad ? -1 : 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Inverse normal CDF (paper silent; reading c7): Newton's method on   */
 /* Phi(x) = erfc(-x / sqrt 2) / 2 with a bisection safeguard, for the  */
 /* lower half q in (0, 1/2].                                           */

@@ -351,6 +351,38 @@ def test_lms_differs_from_the_shift_alone():
     assert np.mean(a != b) > 0.8
 
 
+# ------------------------------------------------------------------ Table 1 CPU generators
+@pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP])
+@pytest.mark.parametrize("n_start", [0, 1, 8191, 123456])
+def test_algorithm2_stream_equals_counter_based(seq, n_start):
+    # Algorithm 2 (recursive odometer with cached suffix sums) and Algorithm 3 (counter-based)
+    # give the same numerators; the runs cross carries of many digits in small bases
+    q = O.Sequence(seq, 30, 2, seed=17)
+    count = 3000
+    got = q.stream(n_start, count, threads=2)
+    ref = q.points(n_start + count, transform=O.RAW)[:, :, n_start:]
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("seq", [O.SOBOL_DS, O.SOBOL_LMS])
+@pytest.mark.parametrize("n_start", [0, 5, 1023, 77777])
+def test_gray_code_stream_is_the_gray_permutation(seq, n_start):
+    # Antonov-Saleev: element c of the stream is the point of index g(n_start + c)
+    q = O.Sequence(seq, 24, 2, seed=3, joe_kuo=inputs.joe_kuo_table())
+    count = 2048
+    got = q.stream(n_start, count, threads=2)
+    for m in range(2):
+        for j in (0, 1, 7, 23):
+            for c in range(0, count, 97):
+                n = n_start + c
+                assert int(got[m, j, c]) == q.raw(m, j, n ^ (n >> 1))[0]
+    # each aligned block of 2^k Gray-order points is the same set as the binary-order block
+    if n_start == 0:
+        ref = q.points(count, transform=O.RAW)
+        for k in (4, 11):
+            assert sorted(got[1, 5, :1 << k].tolist()) == sorted(ref[1, 5, :1 << k].tolist())
+
+
 # ------------------------------------------------------------------ inverse normal
 def test_ndtri_matches_scipy():
     special = pytest.importorskip("scipy.special")
