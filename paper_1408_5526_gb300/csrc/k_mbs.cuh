@@ -1,6 +1,7 @@
 // k_mbs.cuh -- paths of the mortgage-backed-security model (Sec. 6), shared by the MBS
 // kernel and the batched kernel.
 #pragma once
+#include "atan_coeffs.h"
 #include "paths_common.cuh"
 
 namespace rqmc {
@@ -12,7 +13,15 @@ __device__ __forceinline__ float mbs_exp<float>(float x) { return ex2_approx(x);
 template <>
 __device__ __forceinline__ double mbs_exp<double>(double x) { return exp(x); }
 
-__device__ __forceinline__ float mbs_atan(float x) { return atanf(x); }
+// FP32 arctangent without branches: t = min(|x|, 1/|x|) in [0, 1], atan(t) = t P(t^2) with
+// our own fit (fit_atan.py), reflected by atan(a) = pi/2 - atan(1/a) for a > 1.
+__device__ __forceinline__ float mbs_atan(float x) {
+    constexpr float C[] = RQMC_ATAN_C;
+    const float a = fabsf(x);
+    const float t = fminf(a, rcp_approx(a));
+    const float r = t * horner(C, t * t);
+    return copysignf(a > 1.0f ? 1.5707963267948966f - r : r, x);
+}
 __device__ __forceinline__ double mbs_atan(double x) { return atan(x); }
 
 // P paths in lockstep (same arithmetic per path as P = 1): they share the c_k loads and
