@@ -1,9 +1,11 @@
-// k_batch.cuh -- one persistent launch over a batch of heterogeneous instruments (LMM caplet
-// strips of 8..160 forwards and MBS of up to 4096 months), instantiated per sequence by
+// k_batch.cuh -- persistent kernels over a batch of heterogeneous instruments (LMM caplet
+// strips of 8..160 forwards and MBS of up to 4096 months), one kernel per work class
+// (160-forward strips, MBS, smaller strips; see BatchLaunch), instantiated per sequence by
 // k_batch_{halton,sobol,philox}.cu.
 //
 // Work items are (instrument, replication m, tile of consecutive points), listed longest
-// first (LPT).  Each CTA takes the next item with one atomicAdd on a ticket counter -- no
+// first (LPT) per class.  Each CTA takes its class's next item with one atomicAdd on a
+// ticket counter -- no
 // CTA ever waits on another, so the loop cannot deadlock -- stages that instrument's tables
 // for m into shared memory, runs the tile's paths with the same path code as the
 // single-instrument kernels (FP32 paths, Kahan sums) and writes the item's own partial

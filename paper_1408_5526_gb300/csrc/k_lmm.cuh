@@ -122,7 +122,7 @@ constexpr int lmm_min_blocks() {
     return regs <= 64 ? 4 : regs <= 85 ? 3 : regs <= 128 ? 2 : 1;
 }
 
-// P paths in lockstep (P = 1 or 2): forwards in registers, per-step payoffs (summed over
+// P paths in lockstep (1 or 2 in the caplet kernel, up to 4 in the batch): forwards in registers, per-step payoffs (summed over
 // the P paths) into the warp's transpose buffer, block sums into the warp's Kahan
 // accumulators (wacc/wcmp, indexed by output t nK + k).  The P paths share every constant
 // load and all control flow, and give each warp P independent dependency chains.
