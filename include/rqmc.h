@@ -175,7 +175,8 @@ rqmc_status price_adjoint(const rqmc_lmm_params *p, const double *strikes_host, 
 /* Batch of n instruments in one CUDA graph (not in the paper): one persistent kernel per
  * work class (160-forward strips, smaller strips, MBS), each with a longest-first ticket
  * queue, as parallel branches; tiles picked by an autotuner whose choice is cached in
- * $RQMC_AUTOTUNE_CACHE (default ~/.cache/rqmc_gb300/autotune.json; RQMC_AUTOTUNE=0 skips it).  Instrument i uses instrument index i in its Philox counters.  Output
+ * $RQMC_AUTOTUNE_CACHE (default ~/.cache/rqmc_gb300/autotune.json; RQMC_AUTOTUNE=0 skips it).
+ * Instrument i uses instrument index i in its Philox counters.  Output
  * theta_host holds, instrument after instrument, an [M][n_out_i] block with n_out_i =
  * size (LMM) or 1 (MBS). */
 rqmc_status price_batch(const rqmc_instrument *inst, int n, int M, rqmc_sequence seq, uint64_t seed,
