@@ -113,6 +113,8 @@ struct GenParams {
     const uint32_t *sobShift;// [M][s]
     int sob_bits;            // bits of offset + N - 1
     int stage_sig;           // 1: a replication's permutations are staged in shared memory
+    int stage;               // 1: a replication's per-dimension tables are staged in shared
+                             //    memory; 0 (very large s): the kernels read them from global
 };
 
 // Per-replication view of the generator tables used by the path kernels; the tables
@@ -133,6 +135,7 @@ __host__ __device__ __forceinline__ size_t align16(size_t x) { return (x + 15) &
 
 // Shared-memory bytes the staging of one replication's tables takes.
 __host__ __device__ __forceinline__ size_t stage_bytes(const GenParams &g) {
+    if (!g.stage) return 0;
     if (g.seq == kHaltonRS || g.seq == kRasrap)
         return align16(sizeof(HaltonDim) * g.s) + (g.stage_sig ? align16(2 * g.sig_len) : 0);
     if (g.seq == kSobolDS) return align16(4ull * 32 * g.s) + align16(4ull * g.s);
@@ -153,6 +156,16 @@ __device__ __forceinline__ void stage_tables(const GenParams &g, int m, unsigned
     v.sig = nullptr;
     v.V = nullptr;
     v.shift = nullptr;
+    if (!g.stage) {   // tables too large for shared memory: read them where they are
+        if (g.seq == kHaltonRS || g.seq == kRasrap) {
+            v.hd = g.hdim + (size_t)m * g.s;
+            v.sig = g.sigma + (size_t)m * g.sig_len;
+        } else if (g.seq == kSobolDS) {
+            v.V = g.sobV + (size_t)m * g.sobV_mstride;
+            v.shift = g.sobShift + (size_t)m * g.s;
+        }
+        return;
+    }
     if (g.seq == kHaltonRS || g.seq == kRasrap) {
         HaltonDim *hd = reinterpret_cast<HaltonDim *>(sm);
         const uint4 *src = reinterpret_cast<const uint4 *>(g.hdim + (size_t)m * g.s);

@@ -283,6 +283,7 @@ rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint
     g.key1 = (uint32_t)(pl.seed >> 32);
     g.inst = pl.inst;
     g.offset = pl.offset;
+    g.stage = 1;
     const int nthr = 128, nblk = (M * s + nthr - 1) / nthr;
     if (pl.seq == kHaltonRS || pl.seq == kRasrap) {
         g.hdim = reinterpret_cast<const HaltonDim *>(d + gl.hdim_off);
@@ -320,6 +321,10 @@ rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint
         while (bits < 32 && (last >> bits) != 0) ++bits;
         g.sob_bits = bits;
     }
+    // Per-dimension tables of one replication go to shared memory when they fit comfortably
+    // (up to 64 KB: s <= ~800 for Halton, ~490 for Sobol'); beyond, the kernels read them
+    // from global memory (L1/L2-cached), so every s up to the API's limit runs.
+    g.stage = stage_bytes(g) <= 64ull * 1024 ? 1 : 0;
     return cudaGetLastError() == cudaSuccess ? RQMC_OK : RQMC_ECUDA;
 }
 
