@@ -123,8 +123,15 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
             // ---------------- forward sweep
             float disc = md.disc0, value = 0.0f;
             for (int t = 0; t < nf; ++t) {
-                float Az0 = sqhl * Draw<float>::normal(pg, t * D), Az1 = 0.0f, A0 = 0.0f, A1 = 0.0f;
-                if constexpr (D == 2) Az1 = sqhl * Draw<float>::normal(pg, t * D + 1);
+                float Az0, Az1 = 0.0f, A0 = 0.0f, A1 = 0.0f;
+                if constexpr (D == 2) {
+                    float z0, z1;
+                    normals32_two_dims<SEQ>(pg, 2 * t, 2 * t + 1, z0, z1);
+                    Az0 = sqhl * z0;
+                    Az1 = sqhl * z1;
+                } else {
+                    Az0 = sqhl * Draw<float>::normal(pg, t);
+                }
                 const float Xpre = xcol[t * BD];
                 float4 *hdr = rec;
                 rec += T;
@@ -195,8 +202,9 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                     p1 = __ldcs(q);
                     q -= T;
                 }
-                const float Z0 = Draw<float>::normal(pg, t * D);
-                const float Z1 = D == 2 ? Draw<float>::normal(pg, t * D + 1) : 0.0f;
+                float Z0, Z1 = 0.0f;
+                if constexpr (D == 2) normals32_two_dims<SEQ>(pg, 2 * t, 2 * t + 1, Z0, Z1);
+                else Z0 = Draw<float>::normal(pg, t);
                 // post-step value of the fixed forward, with the forward sweep's operations
                 const float4 ct = cfw[t];
                 const int jt = t & 3;

@@ -202,6 +202,41 @@ __device__ __forceinline__ void normals32(PathGen<SEQ> (&pg)[P], int j, float (&
     ndtri32_lockstep<P>(u, z);
 }
 
+// FP32 normals of two dimensions j0, j1 of one path (the values of two Draw<float>::normal
+// calls): the Sobol' bit loop and the Halton digit loops of the two dimensions run together.
+template <int SEQ>
+__device__ __forceinline__ void normals32_two_dims(PathGen<SEQ> &pg, int j0, int j1, float &z0, float &z1) {
+    Unif32 u[2];
+    const GenView &v = pg.v;
+    if constexpr (SEQ == kPhilox) {
+        u[0] = unif32_from_u32(pg.philox_word(j0));
+        u[1] = unif32_from_u32(pg.philox_word(j1));
+    } else if constexpr (SEQ == kSobolDS) {
+        const uint32_t *V0 = v.V + 32 * j0, *V1 = v.V + 32 * j1;
+        const uint32_t n = (uint32_t)pg.n;
+        uint32_t x0 = v.shift[j0], x1 = v.shift[j1];
+#pragma unroll 4
+        for (int k = 0; k < v.sob_bits; ++k) {
+            const bool b = (n >> k) & 1u;
+            x0 ^= b ? V0[k] : 0u;
+            x1 ^= b ? V1[k] : 0u;
+        }
+        u[0] = unif32_from_u32(x0);
+        u[1] = unif32_from_u32(x1);
+    } else {
+        const HaltonDim &h0 = v.hd[j0], &h1 = v.hd[j1];
+        uint32_t c0, c1;
+        const uint32_t R0 = halton_R(h0, v.sig, pg.i, c0);
+        const uint32_t R1 = halton_R(h1, v.sig, pg.i, c1);
+        u[0] = unif32_halton(h0, R0, c0);
+        u[1] = unif32_halton(h1, R1, c1);
+    }
+    float z[2];
+    ndtri32_lockstep<2>(u, z);
+    z0 = z[0];
+    z1 = z[1];
+}
+
 template <typename T>
 __device__ __forceinline__ T fast_exp2(T x);
 template <>
