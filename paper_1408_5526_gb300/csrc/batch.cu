@@ -382,6 +382,11 @@ extern "C" rqmc_status rqmc_plan_batch(const rqmc_instrument *inst, int n, int M
     for (int i = 0; i < n; ++i) {
         rqmc_status rs = generator_init(sub[i], gls[i], d + base[i], status, 0);
         if (rs != RQMC_OK) return fail(rs);
+        if (!sub[i].gen.stage) {   // the batch kernels stage every instrument's tables
+            set_error("batch: instrument " + std::to_string(i) + " has " + std::to_string(inst[i].size) +
+                      " dimensions, more than the batch stages in shared memory; price it with its own plan");
+            return fail(RQMC_EUNSUPPORTED);
+        }
         BatchInst &bi = bp->insts[i];
         bi = BatchInst{};
         bi.g = sub[i].gen;

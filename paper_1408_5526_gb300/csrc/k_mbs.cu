@@ -16,7 +16,7 @@ constexpr int mbs_ilp() {
     return sizeof(T) == 4 ? 2 : 1;
 }
 
-template <typename T, int SEQ>
+template <typename T, int SEQ, bool STAGED>
 __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsModel<T> md, const RedParams r) {
     constexpr int P = mbs_ilp<T>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsMo
         const uint32_t tile = u % r.tiles_per_m;
         if (m != staged_m) {
             __syncthreads();
-            stage_tables(g, m, smem_raw, gv);
+            load_tables<STAGED>(g, m, smem_raw, gv);
             staged_m = m;
         }
         __syncthreads();
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsMo
 
 template <typename T, int SEQ>
 static cudaError_t launch_mbs_t(const Plan &pl, const MbsModel<T> &md, cudaStream_t st) {
-    auto kern = mbs_kernel<T, SEQ>;
+    auto kern = pl.gen.stage ? mbs_kernel<T, SEQ, true> : mbs_kernel<T, SEQ, false>;
     const int threads = pl.threads;
     const size_t smem = stage_bytes(pl.gen) + (2ull * (threads / 32) + md.months + 1) * sizeof(T);
     if (smem > 48 * 1024) {

@@ -4,7 +4,7 @@
 
 namespace rqmc {
 
-template <typename T, int SEQ>
+template <typename T, int SEQ, bool STAGED>
 __global__ void __launch_bounds__(256) product_kernel(const GenParams g, const ProductModel<T> md,
                                                       const RedParams r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -21,7 +21,7 @@ __global__ void __launch_bounds__(256) product_kernel(const GenParams g, const P
         const uint32_t tile = u % r.tiles_per_m;
         if (m != staged_m) {
             __syncthreads();
-            stage_tables(g, m, smem_raw, gv);
+            load_tables<STAGED>(g, m, smem_raw, gv);
             staged_m = m;
         }
         __syncthreads();
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) product_kernel(const GenParams g, const P
 
 template <typename T, int SEQ>
 static cudaError_t launch_product_t(const Plan &pl, const ProductModel<T> &md, cudaStream_t st) {
-    auto kern = product_kernel<T, SEQ>;
+    auto kern = pl.gen.stage ? product_kernel<T, SEQ, true> : product_kernel<T, SEQ, false>;
     const int threads = pl.threads;
     const size_t smem = stage_bytes(pl.gen) + 2ull * (threads / 32) * sizeof(T);
     if (smem > 48 * 1024) {

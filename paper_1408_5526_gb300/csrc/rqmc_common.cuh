@@ -142,7 +142,9 @@ __host__ __device__ __forceinline__ size_t stage_bytes(const GenParams &g) {
     return 0;
 }
 
-// All threads of the CTA call this (no barrier inside; the caller synchronises).
+// All threads of the CTA call this (no barrier inside; the caller synchronises).  Every
+// pointer of the view points into shared memory, which the compiler can see, so the
+// generators' table reads compile to shared-memory loads.
 __device__ __forceinline__ void stage_tables(const GenParams &g, int m, unsigned char *sm, GenView &v) {
     v.seq = g.seq;
     v.s = g.s;
@@ -156,16 +158,6 @@ __device__ __forceinline__ void stage_tables(const GenParams &g, int m, unsigned
     v.sig = nullptr;
     v.V = nullptr;
     v.shift = nullptr;
-    if (!g.stage) {   // tables too large for shared memory: read them where they are
-        if (g.seq == kHaltonRS || g.seq == kRasrap) {
-            v.hd = g.hdim + (size_t)m * g.s;
-            v.sig = g.sigma + (size_t)m * g.sig_len;
-        } else if (g.seq == kSobolDS) {
-            v.V = g.sobV + (size_t)m * g.sobV_mstride;
-            v.shift = g.sobShift + (size_t)m * g.s;
-        }
-        return;
-    }
     if (g.seq == kHaltonRS || g.seq == kRasrap) {
         HaltonDim *hd = reinterpret_cast<HaltonDim *>(sm);
         const uint4 *src = reinterpret_cast<const uint4 *>(g.hdim + (size_t)m * g.s);
@@ -190,6 +182,37 @@ __device__ __forceinline__ void stage_tables(const GenParams &g, int m, unsigned
         v.V = V;
         v.shift = sh;
     }
+}
+
+// View of replication m's tables where they are, in global memory (for s too large to stage;
+// g.stage == 0).  A separate function, so that kernels which stage keep pointers the
+// compiler knows to be shared.
+__device__ __forceinline__ void view_tables(const GenParams &g, int m, GenView &v) {
+    v.seq = g.seq;
+    v.s = g.s;
+    v.sob_bits = g.sob_bits;
+    v.key0 = g.key0;
+    v.key1 = g.key1;
+    v.inst = g.inst;
+    v.m = m;
+    v.offset = g.offset;
+    v.hd = nullptr;
+    v.sig = nullptr;
+    v.V = nullptr;
+    v.shift = nullptr;
+    if (g.seq == kHaltonRS || g.seq == kRasrap) {
+        v.hd = g.hdim + (size_t)m * g.s;
+        v.sig = g.sigma + (size_t)m * g.sig_len;
+    } else if (g.seq == kSobolDS) {
+        v.V = g.sobV + (size_t)m * g.sobV_mstride;
+        v.shift = g.sobShift + (size_t)m * g.s;
+    }
+}
+
+template <bool STAGED>
+__device__ __forceinline__ void load_tables(const GenParams &g, int m, unsigned char *sm, GenView &v) {
+    if constexpr (STAGED) stage_tables(g, m, sm, v);
+    else view_tables(g, m, v);
 }
 
 // ------------------------------------------------------------------ Halton digits
