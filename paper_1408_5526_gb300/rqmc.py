@@ -120,6 +120,17 @@ def _check(L, status):
         raise RqmcError(status, L.rqmc_last_error().decode())
 
 
+def _check_out(t, n: int, dtype, what: str):
+    """A caller's output tensor must hold n elements of dtype, contiguous, on a CUDA device:
+    the library writes through the raw pointer and cannot check it."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{what}: a torch tensor is required")
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() < n:
+        raise ValueError(f"{what}: need a contiguous CUDA {dtype} tensor of at least {n} elements, got "
+                         f"{t.dtype} {tuple(t.shape)} on {t.device}")
+
+
 def _enum(v, table):
     return table[v] if isinstance(v, str) else int(v)
 
@@ -163,6 +174,7 @@ def rqmc_points(s, N, M, seq, seed, offset=0, prec="fp32", transform="uniform", 
     dt = torch.int64 if tr == RAW else (torch.float32 if pr == FP32 else torch.float64)
     if out is None:
         out = torch.empty((M, s, N), dtype=dt, device="cuda")
+    _check_out(out, M * s * N, dt, "rqmc_points out")
     _check(L, L.rqmc_points(s, N, M, _enum(seq, _SEQ), seed, offset, pr, tr, C.c_void_p(out.data_ptr()),
                             _stream(stream)))
     return out
@@ -258,10 +270,12 @@ def price_batch(insts, M, seq, seed, prec="fp32", stream=None):
 def price_caplets_noalloc(lmm: dict, strikes, N, M, seq, seed, theta, prec="fp32", stream=None):
     """Caplet values into the device tensor `theta` [M, n_fwd*n_strikes] (float64) with no
     allocation by the library (scratch is a fixed 16 MiB array inside it); asynchronous."""
+    import torch
     L = load()
     keep: list = []
     p = _lmm_struct(lmm, keep)
     K = np.ascontiguousarray(strikes, dtype=np.float64)
+    _check_out(theta, M * p.n_fwd * len(K), torch.float64, "price_caplets_noalloc theta")
     _check(L, L.rqmc_price_caplets_noalloc(C.byref(p), _dp(K), len(K), N, M, _enum(seq, _SEQ), seed,
                                            _enum(prec, _PREC),
                                            C.cast(C.c_void_p(theta.data_ptr()), C.POINTER(C.c_double)),
@@ -365,6 +379,10 @@ class Plan:
             else:
                 theta = torch.empty(self.output_size(), dtype=torch.float64, device="cuda")
         L = load()
+        if hasattr(self, "points_shape"):
+            _check_out(theta, self.output_size(), getattr(torch, self.points_dtype), "Plan.execute out")
+        else:
+            _check_out(theta, self.output_size(), torch.float64, "Plan.execute theta")
         _check(L, L.rqmc_plan_execute(self._h, C.cast(C.c_void_p(theta.data_ptr()), C.POINTER(C.c_double)),
                                       _stream(stream)))
         return theta
@@ -376,6 +394,13 @@ class Plan:
         if self._h:
             load().rqmc_plan_destroy(self._h)
             self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+        return False
 
     def __del__(self):
         try:

@@ -62,3 +62,17 @@ def test_sobol_table_recurrence_rejects_even_direction_numbers(lib):
     p, v = inputs.joe_kuo_table()
     assert lib.rqmc_set_sobol_table(p.ctypes.data_as(C.POINTER(C.c_int64)),
                                     v.ctypes.data_as(C.POINTER(C.c_int64)), 4096, v.shape[1]) == 0
+
+
+def test_binding_refuses_output_tensors_it_cannot_write_safely():
+    # the C ABI writes through a raw pointer; the binding checks size, dtype, device and
+    # layout of a caller's tensor first
+    import pytest
+    import torch
+    from paper_1408_5526_gb300 import rqmc
+    with pytest.raises(TypeError):
+        rqmc._check_out(np.zeros(8), 8, torch.float64, "t")
+    with pytest.raises(ValueError):                       # host tensor
+        rqmc._check_out(torch.zeros(8, dtype=torch.float64), 8, torch.float64, "t")
+    with pytest.raises(ValueError):                       # wrong dtype (checked before the device)
+        rqmc._check_out(torch.zeros(8, dtype=torch.float32), 8, torch.float64, "t")
