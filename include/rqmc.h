@@ -233,6 +233,9 @@ int64_t rqmc_plan_output_size(const rqmc_plan *plan);
 int rqmc_plan_launches(const rqmc_plan *plan);
 /* Tuning knobs of a plan: threads per block and paths per thread (0 = keep). */
 rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int paths_per_thread);
+/* Launch the plan's kernels on `stream` (asynchronous), writing rqmc_plan_output_size(plan)
+ * values to device memory `theta_dev`, which the caller owns and must size; the device the
+ * plan was built on must be current (RQMC_EINVAL otherwise, nothing launched). */
 rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, void *stream);
 /* Status word of the plan's last execute (synchronises `stream`). */
 rqmc_status rqmc_plan_check(rqmc_plan *plan, void *stream);

@@ -359,6 +359,12 @@ extern "C" rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int pa
 
 extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, void *stream) {
     if (!plan || !theta_dev) { set_error("plan and theta_dev are required"); return RQMC_EINVAL; }
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != plan->device) {   // its tables live there
+        set_error("the plan was built on device " + std::to_string(plan->device) + ", the current device is " +
+                  std::to_string(cur));
+        return RQMC_EINVAL;
+    }
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (plan->kind == kBatch) return batch_execute(*plan, theta_dev, st);
     cudaError_t e;
