@@ -204,7 +204,9 @@ rqmc_status rqmc_price_caplets_noalloc(const rqmc_lmm_params *p, const double *s
 /* Build randomization tables and model constants on the device once; every
  * rqmc_plan_execute then runs only the kernels and writes theta [M][n_out] doubles
  * to device memory `theta_dev` (asynchronous on `stream`).  `offset` shifts the point
- * range to offset..offset+N-1 (shards of one estimate add up exactly). */
+ * range to offset..offset+N-1 (shards of one estimate add up exactly).  A plan owns its
+ * workspace: executes of one plan must be ordered (one stream, or synchronised), while
+ * different plans may run concurrently. */
 rqmc_status rqmc_plan_product(int s, int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
                               const double *a_host, rqmc_precision prec, rqmc_plan **plan);
 rqmc_status rqmc_plan_caplets(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes, int64_t N,
