@@ -213,8 +213,14 @@ def run_ours(args, rank, world):
             "fma_frac": round(a_fma / fma_peak, 4),
             "kernel": "lmm_caplet_kernel<40,float> + theta_kernel",
             "launch_ms": round(per_launch_s * 1e3, 4),
-            "peak_source": "derived: 16 SFU slots / 128 FP32 lanes per SM per clock x 152 SMs x sm_max_mhz "
-                           "(probe: ex2 29.8, rcp 15.1, lg2 15.4 per SM per clock)"}
+            "peak_source": "derived: 16 SFU slots / 128 FP32 lanes per SM per clock x 152 SMs x sm_max_mhz"}
+    if rank == 0:
+        # the same pipes measured on this GPU (rqmc_probe_pipes), next to the derived peak
+        probe = rqmc.probe_pipes()
+        # one SFU issue slot = one rcp or lg2 = two ex2, as the roofline counts them
+        slot_rate = min(probe["rcp"], probe["lg2"], 0.5 * probe["ex2"])
+        roof["probe_per_sm_clk"] = {k: round(v, 2) for k, v in probe.items()}
+        roof["frac_of_probed_sfu"] = round(a_mufu / (slot_rate * 152 * sm_max * 1e6), 4) if slot_rate else None
     extra = other_workloads(args, dev, seed) if (rank == 0 and not args.no_extra) else None
     cpu = cpu_baseline(args) if (rank == 0 and not args.no_cpu) else None
     cpu_gen = cpu_generators() if (rank == 0 and not args.no_cpu) else None

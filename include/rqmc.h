@@ -244,6 +244,12 @@ rqmc_status rqmc_plan_check(rqmc_plan *plan, void *stream);
 rqmc_status rqmc_plan_destroy(rqmc_plan *plan);
 
 /* ---------------------------------------------------------------- diagnostics */
+
+/* Measured issue rates of this GPU's pipes (not in the paper), as operations per SM per
+ * clock at the device's rated clock, written to rates_host[0..4]: ex2.approx, rcp.approx,
+ * lg2.approx, the forward update's pair rcp(1 + ex2(-x)) (counted once), FP32 FMA.
+ * Synchronous on the current device (a few milliseconds); n must be at least 5. */
+rqmc_status rqmc_probe_pipes(double *rates_host, int n);
 const char *rqmc_status_string(rqmc_status st);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char *rqmc_last_error(void);

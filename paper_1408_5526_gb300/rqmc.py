@@ -34,7 +34,7 @@ EXPORTS = ["rqmc_set_sobol_table", "rqmc_points", "rqmc_integrate_product", "pri
            "rqmc_plan_adjoint", "rqmc_plan_batch", "rqmc_plan_output_size", "rqmc_plan_launches",
            "rqmc_plan_set_launch", "rqmc_plan_execute", "rqmc_plan_check", "rqmc_plan_destroy",
            "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version", "rqmc_price_caplets_noalloc",
-           "rqmc_plan_points"]
+           "rqmc_plan_points", "rqmc_probe_pipes"]
 
 
 class RqmcError(RuntimeError):
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
                                         C.c_uint64, C.c_int, C.c_int, pp]
         L.rqmc_plan_batch.argtypes = [C.POINTER(Instrument), C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, pp]
         L.rqmc_plan_points.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, pp]
+        L.rqmc_probe_pipes.argtypes = [dp, C.c_int]
         L.rqmc_plan_output_size.argtypes = [vp]
         L.rqmc_plan_output_size.restype = i64
         L.rqmc_plan_launches.argtypes = [vp]
@@ -162,6 +163,16 @@ def _lmm_struct(lmm: dict, keep: list) -> LmmParams:
 def _mbs_struct(mbs: dict) -> MbsParams:
     return MbsParams(int(mbs["months"]), 0, float(mbs["i0"]), float(mbs["K1"]), float(mbs["K2"]),
                      float(mbs["K3"]), float(mbs["K4"]), float(mbs["sigma"]), float(mbs.get("c", 1.0)))
+
+
+# ------------------------------------------------------------------ diagnostics
+def probe_pipes() -> dict:
+    """Measured issue rates (operations per SM per clock) of ex2, rcp, lg2, the forward
+    update's ex2 + rcp pair and FP32 FMA on the current GPU."""
+    L = load()
+    r = np.zeros(5)
+    _check(L, L.rqmc_probe_pipes(_dp(r), 5))
+    return dict(zip(("ex2", "rcp", "lg2", "ex2_rcp_pair", "ffma"), map(float, r)))
 
 
 # ------------------------------------------------------------------ point stream

@@ -94,3 +94,11 @@ def test_out_of_range_requests_are_refused_before_any_launch(R):
     # a refused request leaves the library usable
     th, _, _ = R.price_caplets(inputs.lmm_flat(8), [0.05], 64, 1, "philox", 1, prec="fp64")
     assert np.all(np.isfinite(th)) and math.isfinite(float(th.sum()))
+
+
+def test_pipe_probe_reports_plausible_rates(R):
+    r = R.probe_pipes()
+    assert set(r) == {"ex2", "rcp", "lg2", "ex2_rcp_pair", "ffma"}
+    assert all(math.isfinite(v) and v > 0 for v in r.values())
+    # per SM per clock: at most the 128 FP32 lanes; the pair is no faster than its rcp
+    assert r["ffma"] <= 140 and r["ex2"] <= 140 and r["ex2_rcp_pair"] <= r["rcp"] * 1.05

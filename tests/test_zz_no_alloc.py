@@ -56,7 +56,7 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     from paper_1408_5526_gb300 import rqmc
     rqmc.load()
     lm = inputs.lmm_flat(160)
-    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    out = torch.empty(64 * 160 * 8, dtype=torch.float64, device="cuda")   # a valid output buffer
     with pytest.raises(rqmc.RqmcError) as e:
         rqmc.price_caplets_noalloc(lm, [0.05] * 8, 1 << 20, 64, rqmc.PHILOX, 1, out)
     assert e.value.status == 1 and "scratch" in str(e.value)
