@@ -49,7 +49,7 @@ def _peaks():
 
 
 def lmm_algorithmic_ops(nf, nK, paths):
-    """Source-level operations of one fused caplet launch (see DESIGN.md).
+    """Source-level operations of one fused caplet launch.
     MUFU: ex2 + rcp per forward update; per step lg2 (inverse CDF) and ex2 + rcp
     (fixed forward and numeraire).  Returned as SFU issue slots: on GB300 ex2 issues at
     32 per SM per clock and rcp/lg2 at 16, so an ex2 counts half a slot.
