@@ -44,8 +44,10 @@
  *     return and serialise with one another through an internal lock.
  *
  * Limits: s <= 4096 dimensions; N >= 1 with offset + N <= 2^32 for Sobol',
- * <= 2^48 for Philox, and for Halton the bound that p_s^L <= 2^31 for the
- * smallest L with p_s^L >= N (N <= 5.8e6 at s = 360); M <= 65535.
+ * <= 2^48 for Philox, and for Halton that every base p_j (j < s) has p_j^L <= 2^31
+ * for the smallest L with p_j^L >= N (the largest N: 2^31 at s = 1, 214358881 = 11^8 at
+ * s = 8, 38950081 = 79^4 at s = 40, 11089567 = 223^3 at s = 160, 1666681 = 1291^2 at
+ * s = 360); M <= 65535.
  */
 #ifndef RQMC_H
 #define RQMC_H
@@ -187,14 +189,17 @@ rqmc_status price_batch(const rqmc_instrument *inst, int n, int M, rqmc_sequence
 /* The caplet values of price_caplets written to theta_dev [M][nf*n_strikes] (device
  * memory), asynchronously on `stream`, WITHOUT allocating anything.  The paper has no
  * counterpart: this entry point serves callers that cannot allocate device memory at the
- * moment they price (inside a CUDA graph capture, inside another framework's allocator
- * callback, or under a no-allocation-after-start-up policy).  Its scratch space is one
- * 16 MiB array built into the library, created on every GPU that loads the library and
- * held until the process exits; a request whose tables and partial sums need more returns
- * RQMC_EINVAL with the size in rqmc_last_error().  The first call on each device looks up
- * that array's device address and caches it: make it before any stream capture starts.
- * All calls share the array, so calls whose work overlaps on the GPU race and must be
- * serialised by the caller.  Same argument limits as price_caplets (one factor). */
+ * moment they price (a callback running inside another framework's device allocator, a
+ * process whose device memory a pool reserved entirely at start-up, or a service whose
+ * policy forbids allocation after start-up).  Its scratch space is one 16 MiB array built
+ * into the library, created on every GPU that loads the library and held until the process
+ * exits; a request whose tables and partial sums need more returns RQMC_EINVAL with the
+ * size in rqmc_last_error().  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress) and caches it.  All calls share the array, so calls whose
+ * work overlaps on the GPU race and must be serialised by the caller.  Same argument checks
+ * and error codes as price_caplets (one factor).  A device-side status (a randomized point
+ * range beyond a Halton start's digits, which cannot happen within these limits) makes every
+ * theta value of the call NaN. */
 rqmc_status rqmc_price_caplets_noalloc(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes,
                                        int64_t N, int M, rqmc_sequence seq, uint64_t seed, rqmc_precision prec,
                                        double *theta_dev, void *stream);
@@ -246,9 +251,12 @@ rqmc_status rqmc_plan_destroy(rqmc_plan *plan);
 /* ---------------------------------------------------------------- diagnostics */
 
 /* Measured issue rates of this GPU's pipes (not in the paper), as operations per SM per
- * clock at the device's rated clock, written to rates_host[0..4]: ex2.approx, rcp.approx,
- * lg2.approx, the forward update's pair rcp(1 + ex2(-x)) (counted once), FP32 FMA.
- * Synchronous on the current device (a few milliseconds); n must be at least 5. */
+ * clock, written to rates_host[0..]: [0] ex2.approx, [1] rcp.approx, [2] lg2.approx, [3] the
+ * forward update's pair rcp(1 + ex2(-x)) (counted once), [4] FP32 FMA, and when n allows
+ * [5] FP64 FMA, [6] the FP64 update pair 1/(1 + exp(-x)) (counted once), [7] the SM clock in
+ * MHz that the probes ran at, measured inside them (cycle counter against the global
+ * nanosecond timer) and used as the clock of every rate.  Synchronous on the current device
+ * (a few milliseconds); n must be at least 5. */
 rqmc_status rqmc_probe_pipes(double *rates_host, int n);
 const char *rqmc_status_string(rqmc_status st);
 /* Text of the last error raised on the calling thread ("" if none). */

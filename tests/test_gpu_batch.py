@@ -1,5 +1,8 @@
 """The batched persistent launch (graph-captured, autotuned tiles) against the FP64
-oracle, instrument by instrument (instrument i uses index i in its Philox counters)."""
+oracle, instrument by instrument (instrument i uses index i in its Philox counters).
+Every caplet and MBS value within 1e-4 of the oracle's, relative to that value: the batch's
+caplets are at or in the money, so the at-the-money scale of the caplet tolerance is the
+value itself."""
 import numpy as np
 import pytest
 
@@ -30,17 +33,20 @@ def R(tmp_path_factory):
     return rqmc
 
 
+def _oracle_one(seq, M, seed, i, d):
+    if d["kind"] == "lmm":
+        lm = inputs.lmm_flat(d["n_fwd"], delta=0.25, rate=d["rate"], vol=d["vol"])
+        q = O.Sequence(seq, d["n_fwd"], M, seed, inst=i, joe_kuo=JK)
+        return O.lmm_caplets(q, lm, [d["strike"]], d["N"], threads=1)
+    q = O.Sequence(seq, d["months"], M, seed, inst=i, joe_kuo=JK)
+    return O.mbs_theta(q, inputs.mbs_paper(d["months"]), d["N"], threads=1)[:, None]
+
+
 def _oracle(seq, M, seed, insts=INSTS):
-    out = []
-    for i, d in enumerate(insts):
-        if d["kind"] == "lmm":
-            lm = inputs.lmm_flat(d["n_fwd"], delta=0.25, rate=d["rate"], vol=d["vol"])
-            q = O.Sequence(seq, d["n_fwd"], M, seed, inst=i, joe_kuo=JK)
-            out.append(O.lmm_caplets(q, lm, [d["strike"]], d["N"]))
-        else:
-            q = O.Sequence(seq, d["months"], M, seed, inst=i, joe_kuo=JK)
-            out.append(O.mbs_theta(q, inputs.mbs_paper(d["months"]), d["N"])[:, None])
-    return out
+    """Oracle theta of every instrument (instruments on host threads, one each)."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(min(O.max_threads(), 16)) as ex:
+        return list(ex.map(lambda a: _oracle_one(seq, M, seed, *a), list(enumerate(insts))))
 
 
 @pytest.mark.parametrize("seq", [O.SOBOL_DS, O.RASRAP, O.PHILOX, O.SOBOL_LMS])
@@ -50,8 +56,7 @@ def test_batch_matches_oracle_per_instrument(R, seq):
     ref = _oracle(seq, M, seed)
     for d, g, r in zip(INSTS, got, ref):
         assert g.shape == r.shape
-        tol = 1e-4 * np.maximum(np.abs(r), np.abs(r).max(axis=1, keepdims=True) * 1e-2) + 1e-12
-        assert np.all(np.abs(g - r) <= tol), (d, np.max(np.abs(g - r) / tol))
+        assert np.all(np.abs(g - r) <= 1e-4 * np.abs(r)), (d, np.max(np.abs(g - r) / np.abs(r)))
 
 
 def test_batch_graph_replay_is_deterministic_and_cached(R):
@@ -79,5 +84,20 @@ def test_batch_with_some_work_classes_empty(R, subset):
     got = R.price_batch(insts, M, O.SOBOL_DS, seed)
     ref = _oracle(O.SOBOL_DS, M, seed, insts)
     for d, g, r in zip(insts, got, ref):
-        tol = 1e-4 * np.maximum(np.abs(r), np.abs(r).max(axis=1, keepdims=True) * 1e-2) + 1e-12
-        assert np.all(np.abs(g - r) <= tol), (d, np.max(np.abs(g - r) / tol))
+        assert np.all(np.abs(g - r) <= 1e-4 * np.abs(r)), (d, np.max(np.abs(g - r) / np.abs(r)))
+
+
+@pytest.mark.parametrize("seq,M", [(O.SOBOL_DS, 2), (O.RASRAP, 1)])
+def test_batch_512_instrument_draw_with_capped_N(R, seq, M):
+    """The 512-instrument draw of the batch workload (384 caplet strips of 8..160 forwards
+    and 128 MBS of 120..360 months, sizes as drawn from seed 1) with every instrument's N
+    capped at 2^11 so that the oracle prices all 512 in well under a minute on the host.
+    All three work classes and the full ticket queues run; each instrument's values are
+    checked against the oracle."""
+    desc = inputs.batch_instruments(1)
+    insts = [dict(d, N=min(d["N"], 1 << 11), rate=0.05, vol=0.15, strike=0.05) if d["kind"] == "lmm"
+             else dict(d, N=min(d["N"], 1 << 11)) for d in desc]
+    got = R.price_batch(insts, M, seq, 1)
+    ref = _oracle(seq, M, 1, insts)
+    worst = max(float(np.max(np.abs(g - r) / np.abs(r))) for g, r in zip(got, ref))
+    assert worst <= 1e-4, worst

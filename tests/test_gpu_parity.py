@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+import oracle_par
 from paper_1408_5526_gb300 import inputs
 
 JK = inputs.joe_kuo_table()
@@ -177,14 +178,65 @@ def test_mbs_small(R, seq):
     np.testing.assert_allclose(th32, th_o, rtol=1e-4)
 
 
-def test_mbs_full_size_sampled(R):
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
+def test_mbs_full_size_sampled(R, seq):
+    """The 360-month, N = 65536, M = 64 MBS workload; the oracle recomputes the last
+    replication at full N (point ranges on host threads)."""
     cfg = inputs.CONFIGS["mbs_360"]
     mb = inputs.mbs_paper(cfg["months"])
     N, M = cfg["N"], cfg["M"]
-    th32, rq, sd = R.price_mbs(mb, N, M, O.RASRAP, cfg["seed"], prec="fp32")
+    th32, rq, sd = R.price_mbs(mb, N, M, seq, cfg["seed"], prec="fp32")
     m = M - 1
-    th_o = O.mbs_theta(O.Sequence(O.RASRAP, 360, M, cfg["seed"]), mb, N, m_range=(m, m + 1))
+    q = O.Sequence(seq, 360, M, cfg["seed"], joe_kuo=JK)
+    th_o = oracle_par.over_points(lambda off, n: O.mbs_theta(q, mb, n, offset=off, m_range=(m, m + 1), threads=1), N)
     np.testing.assert_allclose(th32[m], th_o[0], rtol=1e-4)
+
+
+# ------------------------------------------------------------------ RQ_{M,N} and the sample std
+def _stats_tol(tol_theta, M):
+    """A change of at most e in every theta_N^m moves their mean by at most e and their
+    sample standard deviation by at most e sqrt(M / (M - 1)) (triangle inequality on the
+    centred vector)."""
+    return tol_theta, tol_theta * np.sqrt(M / (M - 1.0))
+
+
+@pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX])
+def test_rq_and_sd_match_the_oracle(R, seq):
+    """RQ_{M,N} (Sec. 1) and the sample standard deviation over the M replications (the
+    error measure of Sec. 5) that the one-shot calls return, against the oracle's
+    rq_stats of its own theta (M >= 2), for the product integrand, caplets and MBS."""
+    # the library's statistics are those of its own theta, to rounding
+    a = inputs.product_weights(8)
+    th, rq, sd = R.rqmc_integrate_product(8, 4096, 32, seq, 1, a, prec="fp64")
+    rq_g, sd_g = O.rq_stats(th)
+    np.testing.assert_allclose(rq, rq_g[0], rtol=1e-14)
+    np.testing.assert_allclose(sd, sd_g[0], rtol=1e-12)
+    # product integrand, FP64 (theta within 1e-13 relative)
+    th_o = O.product_theta(O.Sequence(seq, 8, 32, 1, joe_kuo=JK), 4096, a)
+    rq_o, sd_o = O.rq_stats(th_o)
+    e_rq, e_sd = _stats_tol(1e-13 * np.abs(th_o).max(), 32)
+    assert abs(rq - rq_o[0]) <= e_rq and abs(sd - sd_o[0]) <= e_sd
+    # caplets, FP64 and FP32, M = 8
+    lm = inputs.lmm_flat(40)
+    K = inputs.LMM_STRIKES
+    M = 8
+    th_o = O.lmm_caplets(O.Sequence(seq, 40, M, 3, joe_kuo=JK), lm, K, 1500)
+    rq_o, sd_o = O.rq_stats(th_o)
+    for prec in ("fp64", "fp32"):
+        th, rq, sd = R.price_caplets(lm, K, 1500, M, seq, 3, prec=prec)
+        tol = (1e-11 * np.abs(th_o) + 1e-15) if prec == "fp64" else _caplet_tol(th_o, len(K))
+        e_rq, e_sd = _stats_tol(tol.max(axis=0), M)
+        assert np.all(np.abs(rq - rq_o) <= e_rq) and np.all(np.abs(sd - sd_o) <= e_sd), prec
+        rq_g, sd_g = O.rq_stats(th)
+        np.testing.assert_allclose(rq, rq_g, rtol=1e-14)
+        np.testing.assert_allclose(sd, sd_g, rtol=1e-11)
+    # MBS, FP32, M = 8
+    mb = inputs.mbs_paper(360)
+    th_o = O.mbs_theta(O.Sequence(seq, 360, M, 5, joe_kuo=JK), mb, 700)
+    rq_o, sd_o = O.rq_stats(th_o)
+    th, rq, sd = R.price_mbs(mb, 700, M, seq, 5, prec="fp32")
+    e_rq, e_sd = _stats_tol(1e-4 * np.abs(th_o).max(), M)
+    assert abs(rq - rq_o[0]) <= e_rq and abs(sd - sd_o[0]) <= e_sd
 
 
 # ------------------------------------------------------------------ plans and sharding

@@ -262,3 +262,29 @@ def test_adjoint_matches_central_differences():
         dn["vol"][n] -= h
         fd = (price(up) - price(dn)) / (2 * h)
         np.testing.assert_allclose(vega[:, n], fd, rtol=2e-5, atol=1e-9)
+
+
+# ------------------------------------------------------------------ RQ_{M,N} and the sample std (Sec. 1, Sec. 5)
+def test_rq_stats_closed_forms():
+    """RQ_{M,N} is the mean of the M estimates theta_N^m (Sec. 1); the error measure of
+    Sec. 5 is their sample standard deviation (divisor M - 1).  Closed forms: two values
+    a, b give |a - b| / sqrt 2; the integers 0..M-1 give mean (M-1)/2 and variance
+    M (M+1) / 12; a constant column has zero spread; one replication reports zero."""
+    rq, sd = O.rq_stats(np.array([[1.0, 5.0], [3.0, 5.0]]))
+    np.testing.assert_allclose(rq, [2.0, 5.0], rtol=0, atol=0)
+    np.testing.assert_allclose(sd, [math.sqrt(2.0), 0.0], rtol=1e-15, atol=0)
+    for M in (2, 3, 10, 64):
+        rq, sd = O.rq_stats(np.arange(M, dtype=np.float64))
+        assert rq[0] == (M - 1) / 2
+        assert abs(sd[0] - math.sqrt(M * (M + 1) / 12.0)) <= 1e-14 * sd[0]
+    rq, sd = O.rq_stats(np.array([[0.25, -1.0, 7.0]]))
+    np.testing.assert_array_equal(rq, [0.25, -1.0, 7.0])
+    np.testing.assert_array_equal(sd, [0.0, 0.0, 0.0])
+
+
+def test_rq_stats_match_numpy():
+    """Against numpy's mean and std(ddof=1) on random estimates, column by column."""
+    th = np.random.default_rng(5).normal(0.01, 1e-4, size=(64, 120))
+    rq, sd = O.rq_stats(th)
+    np.testing.assert_allclose(rq, th.mean(axis=0), rtol=1e-14)
+    np.testing.assert_allclose(sd, th.std(axis=0, ddof=1), rtol=1e-12)

@@ -58,6 +58,8 @@ def _worker(rank, world, port, n_total, result_path):
             q = O.Sequence(seq, 8, 3, 5, joe_kuo=JK)
             th = O.lmm_caplets(q, lm, K, cnt, offset=off, threads=1)
             out[name] = shard.combine_theta(torch.from_numpy(np.ascontiguousarray(th)), cnt).numpy()
+            out[name + "_known_total"] = shard.combine_theta(torch.from_numpy(np.ascontiguousarray(th)), cnt,
+                                                             total=n_total).numpy()
             q8 = O.Sequence(seq, 8, 3, 5, joe_kuo=JK)
             tp = O.product_theta(q8, cnt, inputs.product_weights(8), offset=off, threads=1)
             out[name + "_product"] = shard.combine_theta(torch.from_numpy(np.ascontiguousarray(tp)), cnt).numpy()
@@ -78,6 +80,7 @@ def test_two_gloo_ranks_reproduce_the_unsharded_estimate(tmp_path):
         q = O.Sequence(seq, 8, 3, 5, joe_kuo=JK)
         ref = O.lmm_caplets(q, lm, inputs.LMM_STRIKES, n_total, threads=1)
         np.testing.assert_allclose(got[name], ref, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(got[name + "_known_total"], ref, rtol=1e-12, atol=1e-15)
         q8 = O.Sequence(seq, 8, 3, 5, joe_kuo=JK)
         refp = O.product_theta(q8, n_total, inputs.product_weights(8), threads=1)
         np.testing.assert_allclose(got[name + "_product"], refp, rtol=1e-12, atol=1e-15)
@@ -88,3 +91,24 @@ def test_combine_theta_single_process_is_identity():
     assert torch.equal(shard.combine_theta(th, 17), th)
     with pytest.raises(TypeError):
         shard.combine_theta(th.float(), 17)
+
+
+def test_point_range_threads_reproduce_the_oracle():
+    """The test-side helper that runs the oracle over contiguous point ranges on host
+    threads (tests/oracle_par.py) returns the estimate of one sequential call."""
+    import oracle_par
+    lm = inputs.lmm_two_factor(6, seed=2)
+    K = np.array([0.05])
+    w = np.ones(6)
+    for seq in (O.RASRAP, O.SOBOL_DS, O.PHILOX):
+        q = O.Sequence(seq, 12, 2, 3, joe_kuo=JK)
+        ref = O.lmm_adjoint(q, lm, K, w, 1001, threads=1)
+        got = oracle_par.over_points(lambda off, n: O.lmm_adjoint(q, lm, K, w, n, offset=off, threads=1), 1001,
+                                     threads=5)
+        for a, b in zip(got, ref):
+            np.testing.assert_allclose(a, b, rtol=1e-13, atol=1e-17)
+        mb = inputs.mbs_paper(24)
+        q = O.Sequence(seq, 24, 2, 3, joe_kuo=JK)
+        np.testing.assert_allclose(
+            oracle_par.over_points(lambda off, n: O.mbs_theta(q, mb, n, offset=off, threads=1), 777, threads=4),
+            O.mbs_theta(q, mb, 777, threads=1), rtol=1e-13)
