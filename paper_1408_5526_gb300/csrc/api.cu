@@ -46,7 +46,7 @@ struct ModelHost {
     size_t off = 0;
 };
 
-static rqmc_status common_checks(int s, int64_t N, int64_t offset, int M, int seq, int prec) {
+rqmc_status common_checks(int s, int64_t N, int64_t offset, int M, int seq, int prec) {
     if (s < 1 || s > kMaxDims) { set_error("s must be in 1..4096"); return RQMC_EINVAL; }
     if (N < 1 || N > (int64_t(1) << 31)) { set_error("N must be in 1..2^31"); return RQMC_EINVAL; }
     if (offset < 0) { set_error("offset must be >= 0"); return RQMC_EINVAL; }
@@ -56,7 +56,7 @@ static rqmc_status common_checks(int s, int64_t N, int64_t offset, int M, int se
     return RQMC_OK;
 }
 
-static void set_reduction(Plan &pl, int nout, int threads, int ppt) {
+void set_reduction(Plan &pl, int nout, int threads, int ppt) {
     pl.threads = threads;
     pl.ppt = ppt;
     pl.nout = nout;
@@ -127,7 +127,7 @@ static void destroy(Plan *pl, cudaStream_t st) {
     delete pl;
 }
 
-static int lmm_bucket(int nf) {
+int lmm_bucket(int nf) {
     if (nf <= 16) return 16;
     if (nf <= 40) return 40;
     if (nf <= 80) return 80;
@@ -135,7 +135,7 @@ static int lmm_bucket(int nf) {
 }
 
 template <typename T>
-static void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK, int bucket) {
+void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK, int bucket) {
     const double h = p->delta, sh = std::sqrt(p->delta);
     const double sc = sizeof(T) == 4 ? 1.4426950408889634 : 1.0;   // FP32 works in base 2
     md = LmmModel<T>{};
@@ -158,7 +158,10 @@ static void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K,
     }
 }
 
-static rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool adjoint) {
+template void fill_lmm<float>(LmmModel<float> &, const rqmc_lmm_params *, const double *, int, int);
+template void fill_lmm<double>(LmmModel<double> &, const rqmc_lmm_params *, const double *, int, int);
+
+rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool adjoint) {
     if (!p || !p->L0 || !p->vol) { set_error("LMM parameters missing"); return RQMC_EINVAL; }
     if (p->n_fwd < 1 || p->n_fwd > kMaxFwd) { set_error("n_fwd must be in 1..160"); return RQMC_EINVAL; }
     if (p->n_factors < 1 || p->n_factors > 2 || (!adjoint && p->n_factors != 1)) {

@@ -203,6 +203,14 @@ int adjoint_grid(const Plan &pl);
 constexpr int kAdjointThreads = 256;   // CTA size of the adjoint kernel
 int occupancy_blocks(const Plan &pl);
 
+// ---- argument checks and model constants shared by the caplet entry points (api.cu)
+rqmc_status common_checks(int s, int64_t N, int64_t offset, int M, int seq, int prec);
+rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool adjoint);
+template <typename T>
+void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK, int bucket);
+void set_reduction(Plan &pl, int nout, int threads, int ppt);
+int lmm_bucket(int nf);
+
 // ---- errors
 void set_error(const std::string &msg);
 

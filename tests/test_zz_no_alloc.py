@@ -1,10 +1,10 @@
 """rqmc_price_caplets_noalloc against price_caplets.
 
 The no-allocation entry point exists for callers that cannot allocate device memory
-when they price -- code running inside a CUDA graph capture, inside another
-framework's allocator callback, or under a no-allocation-after-start-up policy.  It
-runs the same caplet kernel but keeps its scratch (tables, partial sums, status) in a
-fixed 16 MiB array built into the library.  The test calls it through the C ABI twice
+when they price -- a callback running inside another framework's device allocator, a
+process whose device memory a pool reserved at start-up, or a service that forbids
+allocation after start-up.  It runs the same caplet kernel but keeps its scratch (tables,
+partial sums, status) in a fixed 16 MiB array built into the library.  The test calls it through the C ABI twice
 in a row per sequence, so the second call reuses the array the first one filled, and
 checks each result against the allocating entry point within the FP32 caplet
 tolerance.  This file is collected last so that a failure here comes after every
@@ -60,3 +60,27 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     with pytest.raises(rqmc.RqmcError) as e:
         rqmc.price_caplets_noalloc(lm, [0.05] * 8, 1 << 20, 64, rqmc.PHILOX, 1, out)
     assert e.value.status == 1 and "scratch" in str(e.value)
+
+
+def test_noalloc_refuses_what_price_caplets_refuses_with_the_same_codes():
+    """Both entry points run the same argument checks: a two-factor model, an unknown
+    scheme, too many forwards and M = 0 give the same status from each (called through the
+    C ABI, so that the binding's own checks do not answer first)."""
+    import torch
+    from paper_1408_5526_gb300 import rqmc
+    L = rqmc.load()
+    out = torch.empty(64 * 200 * 8, dtype=torch.float64, device="cuda")
+    K = np.array([0.05])
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    cases = [(inputs.lmm_two_factor(8, seed=1), 2), (dict(inputs.lmm_flat(8), scheme=1), 2),
+             (inputs.lmm_flat(161), 2), (inputs.lmm_flat(8), 0)]
+    for lm, M in cases:
+        keep: list = []
+        p = rqmc._lmm_struct(lm, keep)
+        th = np.zeros(max(M, 1) * lm["n_fwd"])
+        a = L.price_caplets(C.byref(p), K.ctypes.data_as(C.POINTER(C.c_double)), 1, 64, M, rqmc.PHILOX, 1,
+                            rqmc.FP32, th.ctypes.data_as(C.POINTER(C.c_double)), None, None, stream)
+        b = L.rqmc_price_caplets_noalloc(C.byref(p), K.ctypes.data_as(C.POINTER(C.c_double)), 1, 64, M,
+                                         rqmc.PHILOX, 1, rqmc.FP32,
+                                         C.cast(C.c_void_p(out.data_ptr()), C.POINTER(C.c_double)), stream)
+        assert a != 0 and a == b, (lm["n_fwd"], M, a, b)
