@@ -167,12 +167,13 @@ def _mbs_struct(mbs: dict) -> MbsParams:
 
 # ------------------------------------------------------------------ diagnostics
 def probe_pipes() -> dict:
-    """Measured issue rates (operations per SM per clock) of ex2, rcp, lg2, the forward
-    update's ex2 + rcp pair and FP32 FMA on the current GPU."""
+    """Measured issue rates (operations per SM per clock, at the SM clock the probes ran at)
+    of ex2, rcp, lg2, the forward update's ex2 + rcp pair, FP32 FMA, FP64 FMA and the FP64
+    update pair on the current GPU, and that clock in MHz."""
     L = load()
-    r = np.zeros(5)
-    _check(L, L.rqmc_probe_pipes(_dp(r), 5))
-    return dict(zip(("ex2", "rcp", "lg2", "ex2_rcp_pair", "ffma"), map(float, r)))
+    r = np.zeros(8)
+    _check(L, L.rqmc_probe_pipes(_dp(r), 8))
+    return dict(zip(("ex2", "rcp", "lg2", "ex2_rcp_pair", "ffma", "dfma", "fp64_pair", "sm_mhz"), map(float, r)))
 
 
 # ------------------------------------------------------------------ point stream

@@ -74,7 +74,7 @@ def test_very_many_dimensions_read_tables_from_global_memory(R, seq):
     v64, _, _ = R.price_mbs(mb, N, M, seq, 4, prec="fp64")
     np.testing.assert_allclose(v64.reshape(-1), v_o.reshape(-1), rtol=1e-12)
     v32, _, _ = R.price_mbs(mb, N, M, seq, 4, prec="fp32")
-    np.testing.assert_allclose(v32.reshape(-1), v_o.reshape(-1), rtol=5e-4)
+    np.testing.assert_allclose(v32.reshape(-1), v_o.reshape(-1), rtol=1e-4)
     mb1 = inputs.mbs_paper(1)
     v1_o = O.mbs_theta(O.Sequence(seq, 1, 2, 4, joe_kuo=JK), mb1, 500)
     v1, _, _ = R.price_mbs(mb1, 500, 2, seq, 4, prec="fp64")
@@ -98,7 +98,10 @@ def test_out_of_range_requests_are_refused_before_any_launch(R):
 
 def test_pipe_probe_reports_plausible_rates(R):
     r = R.probe_pipes()
-    assert set(r) == {"ex2", "rcp", "lg2", "ex2_rcp_pair", "ffma"}
+    assert set(r) == {"ex2", "rcp", "lg2", "ex2_rcp_pair", "ffma", "dfma", "fp64_pair", "sm_mhz"}
     assert all(math.isfinite(v) and v > 0 for v in r.values())
-    # per SM per clock: at most the 128 FP32 lanes; the pair is no faster than its rcp
+    # per SM per clock: at most the 128 FP32 lanes; the pair is no faster than its rcp; FP64
+    # slower than FP32; the measured clock within the part's range
     assert r["ffma"] <= 140 and r["ex2"] <= 140 and r["ex2_rcp_pair"] <= r["rcp"] * 1.05
+    assert r["dfma"] < r["ffma"] and r["fp64_pair"] < r["dfma"]
+    assert 200 < r["sm_mhz"] < 2300
