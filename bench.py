@@ -6,14 +6,23 @@ forwards, flat 5 % curve, 15 % vol, strikes 4.5/5/5.5 %, log-Euler spot-measure
 steps (s = 40), N = 65536 points per replication, M = 64 replications, on the
 three sequences of the comparison (Rasrap, digitally shifted Sobol', Philox),
 FP32 paths with Kahan sums.  One step = one plan execute per sequence
-(3 x N x M x 40 = 503M path-steps).  The result of every timed configuration is
-checked against the FP64 oracle (two replications at full N) before timing.
+(3 x N x M x 40 = 503M path-steps).
+
+A result counts only when it matches the FP64 oracle in the same run: the
+`cpu_baseline` leg runs the oracle on the host cores over the whole headline
+workload (all 64 replications of all three sequences at full N) and the parity
+block compares every theta_N^m with it (tolerance 1e-4 of the larger of the
+value and the at-the-money caplet of the same maturity).  The other
+configurations of the scope each carry their own timed oracle sample, parity
+check, roofline fraction and error against the oracle.
 
 `--impl reference` times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (the oracle is the reference implementation).
 Under torchrun each rank prices its own contiguous range of N points of every
 replication (plan offset = rank x N, weak scaling); each step ends with the one
-exchange of the estimator, an all-reduce of the M x 120 theta values per sequence.
+exchange of the estimator, a single all-reduce of the 3 x M x 120 theta values
+of the three sequences (the combined counts are known on the host, so nothing is
+read back inside the step).
 """
 from __future__ import annotations
 
@@ -25,6 +34,7 @@ import subprocess
 import sys
 import tempfile
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -35,8 +45,8 @@ N_FWD, N_PATHS, M_REPL, SEED = 40, 65536, 64, 1
 SEQS = ("rasrap", "sobol_ds", "philox")
 L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one lmm_caplet_kernel<40, 1, float> launch
-# (Rasrap) of this workload, from an ncu capture of the kernel as committed; set to None
-# whenever that kernel changes until it is captured again.
+# (Rasrap) of this workload, from an ncu capture of the kernel as committed; None whenever
+# that kernel has changed since the capture.
 LMM_TRAFFIC_BYTES = 714.8e3
 
 
@@ -60,6 +70,39 @@ def lmm_algorithmic_ops(nf, nK, paths):
     slots = 0.5 * n_ex2 + n_rcp + n_lg2
     fma = 4 * upd + nf * (16 + 4 + 4 * nK)
     return slots * paths, fma * paths
+
+
+def lmm_fp64_pairs(nf, paths):
+    """FP64 forward updates of one caplet launch: one exp + one reciprocal per forward update
+    and per fixing (the pair the probe's FP64 update measures)."""
+    return (nf * (nf + 1) // 2 + nf) * paths
+
+
+def mbs_algorithmic_ops(months, paths):
+    """Per month and path: SFU lg2 (inverse CDF), ex2 (rate), rcp (arctangent reflection),
+    rcp (discount) = 3.5 slots; FP32 17 (inverse CDF) + 15 (arctangent) + 16 (rate, prepayment,
+    cash flow, Kahan sum, discount and survival factors) = 48."""
+    return 3.5 * months * paths, 48.0 * months * paths
+
+
+def adjoint_algorithmic_ops(nf, d, paths):
+    """Pathwise adjoint of a d-factor strip, per path: the forward sweep's nf(nf+1)/2 forward
+    updates (ex2 + rcp, 2 + 3d FP32) and the fixings' ex2 + rcp in both sweeps, the reverse
+    sweep's as many adjoint updates (3 + 7d FP32), and 2 nf d inverse CDFs (the normals drawn
+    in the forward sweep and regenerated in the reverse one, lg2 + 17 FP32 each).  SFU slots
+    and FP32 operations."""
+    upd = nf * (nf + 1) // 2
+    slots = 1.5 * (upd + 2 * nf) + 2 * nf * d
+    fma = (2 + 3 * d) * upd + (3 + 7 * d) * upd + 2 * nf * d * 17
+    return slots * paths, fma * paths
+
+
+def caplet_scaled_err(th, th_o, nK):
+    """|theta - theta_oracle| / max(|theta_oracle|, theta_ATM of the same maturity)."""
+    M = th_o.shape[0]
+    t = th_o.reshape(M, -1, nK)
+    scale = np.maximum(np.abs(t), np.abs(t[:, :, nK // 2:nK // 2 + 1])).reshape(M, -1)
+    return np.abs(th.reshape(M, -1) - th_o.reshape(M, -1)) / scale
 
 
 class ClockSampler:
@@ -115,6 +158,48 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+class Peaks:
+    """Roofline denominators on this GPU: SFU issue slots and FP32 lanes derived from the unit
+    counts (16 and 128 per SM per clock) at the maximum SM clock, FP64 rates from the library's
+    own probe, HBM from MEASURED_PEAKS.json."""
+
+    def __init__(self, sms, probe):
+        pk = _peaks()
+        self.sms = sms
+        self.mhz = float(pk.get("sm_max_mhz", 2070.0))
+        self.hbm_gbs = float(pk.get("hbm_gbs", 6800.0))
+        self.hbm_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in pk else "fallback 6.8 TB/s"
+        self.probe = probe
+        self.sfu = 16 * sms * self.mhz * 1e6
+        self.fp32 = 128 * sms * self.mhz * 1e6
+        self.fp64_pair = probe["fp64_pair"] * sms * self.mhz * 1e6
+        self.dfma = probe["dfma"] * sms * self.mhz * 1e6
+
+    def alu(self, slots, fma, seconds, kernel):
+        """Fraction of the busier of the SFU (slots) and FP32 (lanes) pipes."""
+        a_s, a_f = slots / seconds, fma / seconds
+        fs, ff = a_s / self.sfu, a_f / self.fp32
+        sfu = fs >= ff
+        return {"bound": "alu", "pipe": "sfu" if sfu else "fp32",
+                "achieved": round((a_s if sfu else a_f) / 1e12, 4), "peak": round((self.sfu if sfu else self.fp32) / 1e12, 4),
+                "unit": "T SFU issue slots/s" if sfu else "T FP32 lane-ops/s", "frac": round(max(fs, ff), 4),
+                "sfu_frac": round(fs, 4), "fp32_frac": round(ff, 4), "kernel": kernel,
+                "peak_source": f"derived: 16 SFU slots / 128 FP32 lanes per SM per clock x {self.sms} SMs x "
+                               f"{self.mhz:.0f} MHz"}
+
+
+def _oracle_points(fn, N, threads):
+    """An oracle estimate over N points as contiguous point ranges on host threads (ctypes
+    releases the GIL); each part is a mean over its points, weighted by its count."""
+    cuts = np.linspace(0, N, threads + 1).astype(np.int64)
+    rs = [(int(a), int(b - a)) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    with ThreadPoolExecutor(len(rs)) as ex:
+        parts = list(ex.map(lambda r: fn(*r), rs))
+    if isinstance(parts[0], tuple):
+        return tuple(sum(p[k] * c for p, (_, c) in zip(parts, rs)) / N for k in range(len(parts[0])))
+    return sum(p * c for p, (_, c) in zip(parts, rs)) / N
+
+
 def run_ours(args, rank, world):
     import torch
     from paper_1408_5526_gb300 import inputs, rqmc, shard
@@ -122,36 +207,32 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     rqmc.load()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     lm = inputs.lmm_flat(N_FWD)
     K = inputs.LMM_STRIKES
+    nK = len(K)
     seed = SEED
     offset, n_local = shard.point_range(rank, world, N_PATHS * world)
     plans = [rqmc.Plan.caplets(lm, K, n_local, M_REPL, s, seed, prec="fp32", offset=offset) for s in SEQS]
-    outs = [torch.empty(p.output_size(), dtype=torch.float64, device=dev) for p in plans]
+    nout = plans[0].output_size()
+    buf = torch.empty(len(SEQS) * nout, dtype=torch.float64, device=dev)   # the three theta blocks
+    outs = [buf[j * nout:(j + 1) * nout] for j in range(len(SEQS))]
     stream = torch.cuda.current_stream()
 
-    # parity gate: the timed configuration must match the oracle (rank 0 checks)
-    parity = None
-    if rank == 0 and not args.skip_parity:
-        import oracle as O
-        worst = 0.0
-        for p, s, o in zip(plans, SEQS, outs):
-            p.execute(o)
-            th = o.cpu().numpy().reshape(M_REPL, -1)
-            q = O.Sequence(rqmc._SEQ[s], N_FWD, M_REPL, seed, joe_kuo=inputs.joe_kuo_table())
-            th_o = O.lmm_caplets(q, lm, K, N_PATHS, m_range=(M_REPL - 1, M_REPL))
-            t = th_o.reshape(1, N_FWD, len(K))
-            scale = np.maximum(np.abs(t), np.abs(t[:, :, 1:2])).reshape(1, -1)
-            worst = max(worst, float(np.max(np.abs(th[M_REPL - 1:] - th_o) / scale)))
-        parity = {"max_scaled_err": worst, "tol": 1e-4, "ok": worst <= 1e-4, "checked": "m=63, all 120 outputs"}
+    # headline results for the parity gate (the timed loop recomputes them, bit for bit)
+    for p, o in zip(plans, outs):
+        p.execute(o, stream)
+    if world > 1:
+        shard.combine_theta(buf, n_local, total=N_PATHS * world)
+    th_gpu = buf.cpu().numpy().reshape(len(SEQS), M_REPL, -1)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
         for p, o in zip(plans, outs):
             p.execute(o, stream)
-            if world > 1:
-                shard.combine_theta(o, n_local)
+        if world > 1:
+            shard.combine_theta(buf, n_local, total=N_PATHS * world)
 
     for _ in range(args.warmup):
         step()
@@ -170,8 +251,8 @@ def run_ours(args, rank, world):
                 kev[k][j][0].record(stream)
                 p.execute(o, stream)
                 kev[k][j][1].record(stream)
-                if world > 1:
-                    shard.combine_theta(o, n_local)
+            if world > 1:
+                shard.combine_theta(buf, n_local, total=N_PATHS * world)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         time.sleep(0.25)
@@ -184,6 +265,8 @@ def run_ours(args, rank, world):
         total_ms = float(t.item())
     units = N_PATHS * M_REPL * N_FWD * len(SEQS) * args.steps * world
     value = units / (total_ms / 1e3)
+    th_last = buf.cpu().numpy().reshape(len(SEQS), M_REPL, -1)
+    replay_identical = bool(np.array_equal(th_last, th_gpu))
 
     # e2e: the one-shot C-ABI call with host buffers (tables, H2D, kernels, D2H, stats) per sequence
     e2e_ms = []
@@ -195,35 +278,28 @@ def run_ours(args, rank, world):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = N_PATHS * M_REPL * N_FWD * len(SEQS) * world / (statistics.median(e2e_ms) / 1e3)
     h2d = 40 * 64 + 40 * 32 * 4   # Halton base constants (Rasrap) + Sobol' direction numbers
-    d2h = len(SEQS) * (M_REPL * N_FWD * len(K) * 8 + 16)
+    d2h = len(SEQS) * (M_REPL * N_FWD * nK * 8 + 16)
 
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    mufu_peak = 16 * 152 * sm_max * 1e6           # SFU issue slots/s: 16 per SM per clock
-    fma_peak = 128 * 152 * sm_max * 1e6           # FP32 lane-ops/s: 128 per SM per clock
-    mufu, fma = lmm_algorithmic_ops(N_FWD, len(K), N_PATHS * M_REPL)
+    probe = rqmc.probe_pipes()
+    pk = Peaks(sms, probe)
+    mufu, fma = lmm_algorithmic_ops(N_FWD, nK, N_PATHS * M_REPL)
     per_launch_s = statistics.mean(launch_ms) / 1e3
-    a_mufu, a_fma = mufu / per_launch_s, fma / per_launch_s
-    roof = {"bound": "alu", "pipe": "sfu" if a_mufu / mufu_peak >= a_fma / fma_peak else "fma",
-            "achieved": round(a_mufu / 1e12, 4), "peak": round(mufu_peak / 1e12, 4),
-            "unit": "T SFU issue slots/s (ex2 = 1/2 slot, rcp/lg2 = 1 slot)",
-            "frac": round(a_mufu / mufu_peak, 4), "traffic": LMM_TRAFFIC_BYTES,
-            "traffic_unit": "DRAM bytes per launch (ncu, Rasrap launch; tables only)",
-            "fma_achieved": round(a_fma / 1e12, 3), "fma_peak": round(fma_peak / 1e12, 3),
-            "fma_frac": round(a_fma / fma_peak, 4),
-            "kernel": "lmm_caplet_kernel<40,float> + theta_kernel",
-            "launch_ms": round(per_launch_s * 1e3, 4),
-            "peak_source": "derived: 16 SFU slots / 128 FP32 lanes per SM per clock x 152 SMs x sm_max_mhz"}
-    if rank == 0:
-        # the same pipes measured on this GPU (rqmc_probe_pipes), next to the derived peak
-        probe = rqmc.probe_pipes()
-        # one SFU issue slot = one rcp or lg2 = two ex2, as the roofline counts them
-        slot_rate = min(probe["rcp"], probe["lg2"], 0.5 * probe["ex2"])
-        roof["probe_per_sm_clk"] = {k: round(v, 2) for k, v in probe.items()}
-        roof["frac_of_probed_sfu"] = round(a_mufu / (slot_rate * 152 * sm_max * 1e6), 4) if slot_rate else None
-    extra = other_workloads(args, dev, seed) if (rank == 0 and not args.no_extra) else None
-    cpu = cpu_baseline(args) if (rank == 0 and not args.no_cpu) else None
-    cpu_gen = cpu_generators() if (rank == 0 and not args.no_cpu) else None
+    roof = pk.alu(mufu, fma, per_launch_s, "lmm_caplet_kernel<40,SEQ,float> + theta_kernel")
+    roof.update({"traffic": LMM_TRAFFIC_BYTES,
+                 "traffic_unit": "DRAM bytes per launch (ncu, Rasrap launch; tables only)" if LMM_TRAFFIC_BYTES
+                 else "not captured since the kernel last changed",
+                 "launch_ms": round(per_launch_s * 1e3, 4),
+                 "probe_per_sm_clk": {k: round(v, 2) for k, v in probe.items()}})
+    # the same pipes measured on this GPU: one slot = one rcp or lg2 = two ex2
+    slot_rate = min(probe["rcp"], probe["lg2"], 0.5 * probe["ex2"])
+    roof["frac_of_probed_sfu"] = round(mufu / per_launch_s / (slot_rate * sms * pk.mhz * 1e6), 4)
+
+    cpu, parity = None, None
+    if rank == 0 and not args.no_cpu:
+        cpu, parity = headline_oracle(th_gpu, lm, K, args.threads)
+        parity["replay_bit_identical"] = replay_identical
+    extra = other_workloads(args, dev, seed, pk) if (rank == 0 and not args.no_extra) else None
+    cpu_gen = cpu_generators(args.threads) if (rank == 0 and not args.no_cpu) else None
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -236,7 +312,8 @@ def run_ours(args, rank, world):
                        "precision": "fp32 paths, Kahan sums, fp64 replication reduction",
                        "path_steps_per_step": N_PATHS * M_REPL * N_FWD * len(SEQS) * world,
                        "parallelism": (f"point ranges x{world}: offset = rank x N, "
-                                       "theta all-reduced per sequence per step") if world > 1 else "1 GPU",
+                                       "one all-reduce of the three theta blocks per step") if world > 1 else "1 GPU",
+                       "sms": sms,
                        "l2": "flushed (512 MiB write) before every timed step, outside its interval",
                        "timing": "sum of per-step CUDA-event intervals"},
             "parity": parity,
@@ -253,6 +330,36 @@ def run_ours(args, rank, world):
         print(json.dumps(line), flush=True)
     for p in plans:
         p.close()
+
+
+def headline_oracle(th_gpu, lm, K, threads):
+    """The oracle over the whole headline workload (every replication of every sequence at
+    full N, OpenMP over replications): its timing is the CPU baseline and its theta the
+    parity reference of every GPU theta_N^m."""
+    import oracle as O
+    from paper_1408_5526_gb300 import inputs
+    jk = inputs.joe_kuo_table()
+    ids = {"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX}
+    per_seq, t_total = {}, 0.0
+    worst = 0.0
+    for j, s in enumerate(SEQS):
+        q = O.Sequence(ids[s], N_FWD, M_REPL, SEED, joe_kuo=jk)
+        t0 = time.perf_counter()
+        th_o = O.lmm_caplets(q, lm, K, N_PATHS, threads=threads)
+        t_total += time.perf_counter() - t0
+        e = caplet_scaled_err(th_gpu[j], th_o, len(K))
+        rel = np.abs(th_gpu[j] - th_o) / np.abs(th_o)
+        per_seq[s] = {"max_scaled_err": float(e.max()), "max_rel_err": float(rel.max()),
+                      "median_rel_err": float(np.median(rel)), "theta_checked": int(e.size)}
+        worst = max(worst, float(e.max()))
+    steps = len(SEQS) * M_REPL * N_PATHS * N_FWD
+    cpu = {"value": steps / t_total, "unit": "path-steps/s", "cores": threads, "kind": "oracle",
+           "sample": f"the whole workload: 3 sequences x {M_REPL} replications x N={N_PATHS} x {N_FWD} steps "
+                     f"({t_total:.1f} s, OpenMP over replications)"}
+    parity = {"ok": worst <= 1e-4, "tol": 1e-4, "max_scaled_err": worst, "per_sequence": per_seq,
+              "checked": f"every theta_N^m: {M_REPL} replications x {N_FWD * len(K)} outputs x 3 sequences at full N",
+              "scale": "max(|theta_oracle|, theta_oracle of the at-the-money strike, same maturity)"}
+    return cpu, parity
 
 
 def _time_plan(execute, reps, flush):
@@ -272,60 +379,164 @@ def _time_plan(execute, reps, flush):
     return statistics.median(ms)
 
 
-def other_workloads(args, dev, seed):
+def _timed_oracle(fn):
+    t0 = time.perf_counter()
+    r = fn()
+    return r, time.perf_counter() - t0
+
+
+def other_workloads(args, dev, seed, pk):
     """The other configurations of the scope, one timed figure each (median of a few
-    launches, L2 flushed before each, inputs resident): product integrand (FP64),
-    LMM caplets in FP64, MBS (FP32), two-factor adjoint Greeks (FP32), the
-    512-instrument batch (FP32, graph launch), the Treasury-curve study of Sec. 5 (std, time
-    and efficiency against N) and the point stream (HBM write GB/s)."""
+    launches, L2 flushed before each, inputs resident), each with a timed oracle sample
+    (cpu_baseline), the parity of the GPU result on that sample, the largest error against
+    the oracle, and a roofline fraction: product integrand (FP64), LMM caplets in FP64,
+    MBS (FP32), two-factor adjoint Greeks (FP32), the 512-instrument batch (FP32, graph
+    launch), the Treasury-curve study of Sec. 5 (std, time and efficiency against N), the
+    Matousek-scrambled Sobol' caplets and the point stream (HBM write GB/s)."""
     import torch
+
+    import oracle as O
     from paper_1408_5526_gb300 import inputs, rqmc
+    jk = inputs.joe_kuo_table()
+    T = args.threads
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
-    # product integrand, s = 8, N = 4096, M = 32, random-start Halton, FP64
-    p = rqmc.Plan.product(8, 4096, 32, "halton_rs", seed, inputs.product_weights(8), prec="fp64")
+
+    # ---- product integrand, s = 8, N = 4096, M = 32, random-start Halton, FP64
+    s, N, M = 8, 4096, 32
+    a = inputs.product_weights(s)
+    p = rqmc.Plan.product(s, N, M, "halton_rs", seed, a, prec="fp64")
     o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
     ms = _time_plan(lambda: p.execute(o), 10, flush)
     th = o.cpu().numpy()
-    out["product_s8_N4096_M32_fp64"] = {"ms": ms, "path_steps_per_s": 8 * 4096 * 32 / (ms / 1e3),
-                                        "rq": float(th.mean()), "exact": 1.0}
     p.close()
-    # LMM caplets in FP64 (same 40-forward workload), Rasrap
+    th_o, t_o = _timed_oracle(lambda: O.product_theta(O.Sequence(O.HALTON_RS, s, M, seed), N, a, threads=T))
+    rel = float(np.max(np.abs(th - th_o) / np.abs(th_o)))
+    out["product_s8_N4096_M32_fp64"] = {
+        "ms": ms, "path_steps_per_s": s * N * M / (ms / 1e3), "rq": float(th.mean()), "exact": 1.0,
+        "parity": {"ok": rel <= 1e-11, "tol": 1e-11, "max_rel_err": rel, "checked": "all 32 replications"},
+        "cpu_baseline": {"value": s * N * M / t_o, "unit": "point-dims/s", "cores": T, "kind": "oracle",
+                         "sample": "the whole workload"},
+        "roofline": {"bound": "latency", "note": "one launch of 1M point-dims plus the theta reduction; at "
+                     f"{ms * 1e3:.0f} us the launch and tail dominate", "frac": None}}
+
+    # ---- LMM caplets in FP64 (same 40-forward workload), Rasrap
     lm = inputs.lmm_flat(N_FWD)
-    p = rqmc.Plan.caplets(lm, inputs.LMM_STRIKES, N_PATHS, M_REPL, "rasrap", seed, prec="fp64")
+    K = inputs.LMM_STRIKES
+    p = rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, "rasrap", seed, prec="fp64")
     o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
     ms = _time_plan(lambda: p.execute(o), 2, flush)
-    out["lmm_caplets_40_N65536_M64_fp64_rasrap"] = {"ms": ms,
-                                                    "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3)}
+    th = o.cpu().numpy().reshape(M_REPL, -1)
     p.close()
-    # MBS, 360 months, N = 65536, M = 64, FP32 + Kahan
+    mr = 4
+    th_o, t_o = _timed_oracle(lambda: O.lmm_caplets(O.Sequence(O.RASRAP, N_FWD, M_REPL, seed), lm, K, N_PATHS,
+                                                    m_range=(0, mr), threads=T))
+    rel = float(np.max(np.abs(th[:mr] - th_o) / np.abs(th_o)))
+    pairs = lmm_fp64_pairs(N_FWD, N_PATHS * M_REPL)
+    out["lmm_caplets_40_N65536_M64_fp64_rasrap"] = {
+        "ms": ms, "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3),
+        "parity": {"ok": rel <= 1e-11, "tol": 1e-11, "max_rel_err": rel, "checked": f"replications 0..{mr - 1}, full N"},
+        "cpu_baseline": {"value": mr * N_PATHS * N_FWD / t_o, "unit": "path-steps/s", "cores": min(T, mr),
+                         "kind": "oracle", "sample": f"{mr} replications x N={N_PATHS}"},
+        "roofline": {"bound": "fp64", "pipe": "fp64 update pair (exp + reciprocal)",
+                     "achieved": round(pairs / (ms / 1e3) / 1e9, 3), "peak": round(pk.fp64_pair / 1e9, 3),
+                     "unit": "G FP64 update pairs/s", "frac": round(pairs / (ms / 1e3) / pk.fp64_pair, 4),
+                     "peak_source": f"probed: {pk.probe['fp64_pair']:.3f} pairs per SM per clock x {pk.sms} SMs x "
+                                    f"{pk.mhz:.0f} MHz"}}
+
+    # ---- MBS, 360 months, N = 65536, M = 64, FP32 + Kahan
     mb = inputs.mbs_paper(360)
     res = {}
+    ids = {"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX}
     for s_ in SEQS:
         p = rqmc.Plan.mbs(mb, N_PATHS, M_REPL, s_, seed, prec="fp32")
         o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
         ms = _time_plan(lambda: p.execute(o), 3, flush)
-        res[s_] = {"ms": ms, "path_steps_per_s": N_PATHS * M_REPL * 360 / (ms / 1e3), "rq": float(o.mean())}
+        th = o.cpu().numpy()
         p.close()
+        q = O.Sequence(ids[s_], 360, M_REPL, seed, joe_kuo=jk)
+        th_o, t_o = _timed_oracle(lambda: _oracle_points(
+            lambda off, n: O.mbs_theta(q, mb, n, offset=off, m_range=(0, 1), threads=1), N_PATHS, T))
+        rel = float(abs(th[0] - th_o[0]) / abs(th_o[0]))
+        slots, fma = mbs_algorithmic_ops(360, N_PATHS * M_REPL)
+        res[s_] = {"ms": ms, "path_steps_per_s": N_PATHS * M_REPL * 360 / (ms / 1e3), "rq": float(th.mean()),
+                   "parity": {"ok": rel <= 1e-4, "tol": 1e-4, "max_rel_err": rel,
+                              "checked": "replication 0 at full N"},
+                   "cpu_baseline": {"value": N_PATHS * 360 / t_o, "unit": "path-steps/s", "cores": T,
+                                    "kind": "oracle", "sample": f"replication 0 x N={N_PATHS} (point ranges)"},
+                   "roofline": pk.alu(slots, fma, ms / 1e3, f"mbs_kernel<float,{s_}>")}
     out["mbs_360_N65536_M64_fp32"] = res
-    # adjoint Greeks: two-factor 80-forward strip, N = 2^18, M = 32, FP32 paths
-    l2 = inputs.lmm_two_factor(80, seed=seed)
-    p = rqmc.Plan.adjoint(l2, [0.05], np.ones(80), 1 << 18, 32, "sobol_ds", seed)
+
+    # ---- adjoint Greeks: two-factor 80-forward strip, N = 2^18, M = 32, FP32 paths
+    cfg = inputs.CONFIGS["adjoint_2f_80"]
+    l2 = inputs.lmm_two_factor(cfg["n_fwd"], seed=cfg["seed"])
+    Na, Ma, nfa = cfg["N"], cfg["M"], cfg["n_fwd"]
+    w = np.ones(nfa)
+    p = rqmc.Plan.adjoint(l2, [0.05], w, Na, Ma, "sobol_ds", seed)
     o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
     ms = _time_plan(lambda: p.execute(o), 2, flush)
-    out["adjoint_2f_80_N262144_M32_fp32_sobol"] = {"ms": ms,
-                                                   "path_steps_per_s": (1 << 18) * 32 * 160 / (ms / 1e3)}
+    ad = o.cpu().numpy().reshape(Ma, -1)
     p.close()
-    # 512-instrument batch, one graph launch
+    q = O.Sequence(O.SOBOL_DS, 2 * nfa, Ma, seed, joe_kuo=jk)
+    (v_o, d_o, g_o), t_o = _timed_oracle(lambda: _oracle_points(
+        lambda off, n: O.lmm_adjoint(q, l2, [0.05], w, n, offset=off, m_range=(0, 1), threads=1), Na, T))
+    e_v = float(abs(ad[0, 0] - v_o[0]) / abs(v_o[0]))
+    e_d = float(np.max(np.abs(ad[0, 1:1 + nfa] - d_o[0]) / np.abs(d_o[0])))
+    e_g = float(np.max(np.abs(ad[0, 1 + nfa:1 + 2 * nfa] - g_o[0]) / np.abs(g_o[0])))
+    slots, fma = adjoint_algorithmic_ops(nfa, 2, Na * Ma)
+    out["adjoint_2f_80_N262144_M32_fp32_sobol"] = {
+        "ms": ms, "path_steps_per_s": Na * Ma * 2 * nfa / (ms / 1e3),
+        "parity": {"ok": max(e_v, e_d, e_g) <= 1e-4, "tol": 1e-4, "value_rel_err": e_v, "max_delta_rel_err": e_d,
+                   "max_vega_rel_err": e_g, "checked": "replication 0 at full N: value, 80 deltas, 80 vegas"},
+        "cpu_baseline": {"value": Na * 2 * nfa / t_o, "unit": "path-steps/s", "cores": T, "kind": "oracle",
+                         "sample": f"replication 0 x N={Na} (point ranges)"},
+        "roofline": pk.alu(slots, fma, ms / 1e3, "lmm_adjoint_kernel<80,2,sobol>")}
+
+    # ---- 512-instrument batch, one graph launch
     desc = inputs.batch_instruments(seed)
     insts = [dict(d, rate=0.05, vol=0.15, strike=0.05) if d["kind"] == "lmm" else d for d in desc]
-    p = rqmc.Plan.batch(insts, 32, "sobol_ds", seed)
+    Mb = 32
+    p = rqmc.Plan.batch(insts, Mb, "sobol_ds", seed)
     o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
     ms = _time_plan(lambda: p.execute(o), 1, flush)
-    steps = sum(d["N"] * 32 * (d["n_fwd"] if d["kind"] == "lmm" else d["months"]) for d in desc)
-    out["batch_512_M32_fp32_sobol"] = {"ms": ms, "path_steps_per_s": steps / (ms / 1e3), "path_steps": steps}
+    parts = p.split_batch(o.cpu().numpy())
+    imb = p.batch_imbalance() if hasattr(p, "batch_imbalance") else None
     p.close()
-    # Sec. 5's Treasury-curve study: caplet on L_10 (T = 5, delta = 0.5, K = 1 %, sigma = 4 %)
+    steps = sum(d["N"] * Mb * (d["n_fwd"] if d["kind"] == "lmm" else d["months"]) for d in desc)
+    slots = fma = 0.0
+    for d in desc:
+        if d["kind"] == "lmm":
+            s_, f_ = lmm_algorithmic_ops(d["n_fwd"], 1, d["N"] * Mb)
+        else:
+            s_, f_ = mbs_algorithmic_ops(d["months"], d["N"] * Mb)
+        slots, fma = slots + s_, fma + f_
+    sample = list(range(0, len(desc), 32))   # every 32nd instrument, replication 0, full N
+
+    def one(i):
+        d = insts[i]
+        if d["kind"] == "lmm":
+            lmi = inputs.lmm_flat(d["n_fwd"], delta=0.25, rate=d["rate"], vol=d["vol"])
+            return O.lmm_caplets(O.Sequence(O.SOBOL_DS, d["n_fwd"], Mb, seed, inst=i, joe_kuo=jk), lmi, [d["strike"]],
+                                 d["N"], m_range=(0, 1), threads=1)[0]
+        return O.mbs_theta(O.Sequence(O.SOBOL_DS, d["months"], Mb, seed, inst=i, joe_kuo=jk),
+                           inputs.mbs_paper(d["months"]), d["N"], m_range=(0, 1), threads=1)
+
+    def run_sample():
+        with ThreadPoolExecutor(T) as ex:
+            return list(ex.map(one, sample))
+    ref, t_o = _timed_oracle(run_sample)
+    rel = max(float(np.max(np.abs(parts[i][0] - r) / np.abs(r))) for i, r in zip(sample, ref))
+    o_steps = sum(desc[i]["N"] * (desc[i]["n_fwd"] if desc[i]["kind"] == "lmm" else desc[i]["months"]) for i in sample)
+    out["batch_512_M32_fp32_sobol"] = {
+        "ms": ms, "path_steps_per_s": steps / (ms / 1e3), "path_steps": steps,
+        "imbalance_max_sm_busy_over_mean": imb,
+        "parity": {"ok": rel <= 1e-4, "tol": 1e-4, "max_rel_err": rel,
+                   "checked": f"{len(sample)} instruments (every 32nd), replication 0, full N"},
+        "cpu_baseline": {"value": o_steps / t_o, "unit": "path-steps/s", "cores": T, "kind": "oracle",
+                         "sample": f"{len(sample)} instruments x replication 0"},
+        "roofline": pk.alu(slots, fma, ms / 1e3, "batch_kernel<sobol, 3 work classes>")}
+
+    # ---- Sec. 5's Treasury-curve study: caplet on L_10 (T = 5, delta = 0.5, K = 1 %, sigma = 4 %)
     # from the 24 Feb 2012 curve; std of M = 100 independent estimates, time and efficiency
     # (std x time) against N, and the fitted convergence rate of the std
     st = inputs.TREASURY_STUDY
@@ -337,77 +548,94 @@ def other_workloads(args, dev, seed):
             pt = rqmc.Plan.caplets(lmt, [st["K"]], 1 << e, st["M"], s_, seed, prec="fp32")
             ot = torch.empty(pt.output_size(), dtype=torch.float64, device=dev)
             ms = _time_plan(lambda: pt.execute(ot), 3, flush)
-            th = ot.cpu().numpy().reshape(st["M"], -1)[:, lmt["n_fwd"] - 1]
+            th_all = ot.cpu().numpy().reshape(st["M"], -1)
+            th = th_all[:, lmt["n_fwd"] - 1]
             pt.close()
             rows.append({"N": 1 << e, "rq": float(th.mean()), "std": float(th.std(ddof=1)), "ms": ms,
                          "efficiency": float(th.std(ddof=1)) * ms})
+            if e == 14:   # parity at N = 2^14: every replication, the study's caplet and the whole strip
+                sid = {"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX, "sobol_lms": O.SOBOL_LMS}[s_]
+                th_o = O.lmm_caplets(O.Sequence(sid, lmt["n_fwd"], st["M"], seed, joe_kuo=jk), lmt, [st["K"]],
+                                     1 << e, threads=T)
+                c = lmt["n_fwd"] - 1
+                rel14 = float(np.max(np.abs(th_all[:, c] - th_o[:, c]) / np.abs(th_o[:, c])))
+                abs14 = float(np.max(np.abs(th_all - th_o)))
+                ok14 = rel14 <= 1e-4 and bool(np.all(np.abs(th_all - th_o) <= 1e-4 * np.abs(th_o) + 1e-9))
         lx = np.log([r["N"] for r in rows])
         ly = np.log([r["std"] for r in rows])
-        study[s_] = {"rate": float(np.polyfit(lx, ly, 1)[0]), "by_N": rows}
+        study[s_] = {"rate": float(np.polyfit(lx, ly, 1)[0]), "by_N": rows,
+                     "parity": {"ok": ok14, "tol": "1e-4 relative on the study's caplet (L_10); 1e-4 |theta| + 1e-9 "
+                                "on every caplet of the strip (the early ones are worth 0 at K = 1 %)",
+                                "study_caplet_max_rel_err": rel14, "strip_max_abs_err": abs14,
+                                "checked": "N = 2^14, all 100 replications, all 10 caplets"}}
     out["lmm_treasury_study_T5_M100_fp32"] = study
-    # Matousek-scrambled Sobol' on the headline caplet workload (same kernel, scrambled tables)
-    pl_ = rqmc.Plan.caplets(inputs.lmm_flat(N_FWD), inputs.LMM_STRIKES, N_PATHS, M_REPL, "sobol_lms", seed,
-                            prec="fp32")
+
+    # ---- Matousek-scrambled Sobol' on the headline caplet workload (same kernel, scrambled tables)
+    pl_ = rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, "sobol_lms", seed, prec="fp32")
     o_ = torch.empty(pl_.output_size(), dtype=torch.float64, device=dev)
     ms = _time_plan(lambda: pl_.execute(o_), 3, flush)
+    th = o_.cpu().numpy().reshape(M_REPL, -1)
     pl_.close()
-    out["lmm_caplets_40_N65536_M64_fp32_sobol_lms"] = {"ms": ms,
-                                                       "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3)}
-    # point stream: s = 360, N = 65536, M = 64 FP32 normals, written to HBM
+    th_o, t_o = _timed_oracle(lambda: O.lmm_caplets(O.Sequence(O.SOBOL_LMS, N_FWD, M_REPL, seed, joe_kuo=jk), lm, K,
+                                                    N_PATHS, m_range=(0, 4), threads=T))
+    e = float(caplet_scaled_err(th[:4], th_o, len(K)).max())
+    mufu, fma = lmm_algorithmic_ops(N_FWD, len(K), N_PATHS * M_REPL)
+    out["lmm_caplets_40_N65536_M64_fp32_sobol_lms"] = {
+        "ms": ms, "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3),
+        "parity": {"ok": e <= 1e-4, "tol": 1e-4, "max_scaled_err": e, "checked": "replications 0..3, full N"},
+        "cpu_baseline": {"value": 4 * N_PATHS * N_FWD / t_o, "unit": "path-steps/s", "cores": min(T, 4),
+                         "kind": "oracle", "sample": f"4 replications x N={N_PATHS}"},
+        "roofline": pk.alu(mufu, fma, ms / 1e3, "lmm_caplet_kernel<40,sobol,float>")}
+
+    # ---- point stream: s = 360, N = 65536, M = 64 FP32 normals and uniforms, written to HBM
     buf = torch.empty((M_REPL, 360, N_PATHS), dtype=torch.float32, device=dev)
     res = {}
-    peaks = _peaks()
     for s_ in SEQS:
-        pp = rqmc.Plan.points(360, N_PATHS, M_REPL, s_, seed, prec="fp32", transform="normal")
-        ms = _time_plan(lambda: pp.execute(buf), 3, flush)   # kernel only: tables built once
-        pp.close()
+        row = {}
+        for tr in ("normal", "uniform"):
+            pp = rqmc.Plan.points(360, N_PATHS, M_REPL, s_, seed, prec="fp32", transform=tr)
+            ms = _time_plan(lambda: pp.execute(buf), 3, flush)   # kernel only: tables built once
+            pp.close()
+            gbs = buf.numel() * 4 / (ms / 1e3) / 1e9
+            q = O.Sequence(ids[s_], 360, 1, seed, joe_kuo=jk)
+            ref = q.points(4096, transform=O.NORMAL if tr == "normal" else O.UNIFORM, threads=T)[0, :, :]
+            got = buf[0, :, :4096].cpu().numpy().astype(np.float64)
+            err = float(np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref)))) if tr == "normal" else \
+                float(np.max(np.abs(got - ref) / ref))
+            tol = 1e-6 if tr == "normal" else 4e-7
+            row[tr] = {"ms": ms, "GB_per_s": gbs, "gnumbers_per_s": buf.numel() / (ms / 1e3) / 1e9,
+                       "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk.hbm_gbs, "unit": "GB/s",
+                                    "frac": round(gbs / pk.hbm_gbs, 4), "peak_source": pk.hbm_src},
+                       "parity": {"ok": err <= tol, "tol": tol, "max_err": err,
+                                  "checked": "replication 0, all 360 dimensions, points 0..4095"}}
         ms1 = _time_plan(lambda: rqmc.rqmc_points(360, N_PATHS, M_REPL, s_, seed, transform="normal", out=buf), 2,
                          flush)   # one-shot call: tables + kernel
-        gbs = buf.numel() * 4 / (ms / 1e3) / 1e9
-        res[s_] = {"ms": ms, "GB_per_s": gbs, "frac_of_measured_hbm": gbs / float(peaks.get("hbm_gbs", 6800.0)),
-                   "gnumbers_per_s": buf.numel() / (ms / 1e3) / 1e9, "one_shot_ms": ms1}
-    out["points_s360_N65536_M64_fp32_normal"] = res
+        row["one_shot_normal_ms"] = ms1
+        res[s_] = row
+    out["points_s360_N65536_M64_fp32"] = res
     del buf
     return out
 
 
-def cpu_baseline(args, seconds_hint=True):
-    """The FP64 oracle as it stands, OpenMP over replications, on a bounded sample:
-    Rasrap, full N, one replication per host thread (capped at 16)."""
-    import oracle as O
-    from paper_1408_5526_gb300 import inputs
-    cores = min(O.max_threads(), 16)
-    lm = inputs.lmm_flat(N_FWD)
-    K = inputs.LMM_STRIKES
-    q = O.Sequence(O.RASRAP, N_FWD, M_REPL, SEED)
-    t0 = time.perf_counter()
-    O.lmm_caplets(q, lm, K, N_PATHS, m_range=(0, cores), threads=cores)
-    dt = time.perf_counter() - t0
-    return {"value": cores * N_PATHS * N_FWD / dt, "unit": "path-steps/s", "cores": cores, "kind": "oracle",
-            "sample": f"rasrap, {cores} replications x N={N_PATHS} x 40 steps ({dt:.1f} s)"}
-
-
-def cpu_generators():
+def cpu_generators(threads):
     """Table 1 style CPU generator throughput on this host, for context beside the GPU point
     stream: the recursive generators (Algorithm 2 for Rasrap, Gray-code order for Sobol')
     and the counter-based forms (Algorithm 3, binary-order Sobol', Philox) of the oracle,
-    raw integer states of s = 40 dimensions, M = 8, N = 65536, one thread and all threads
-    (capped at 16)."""
+    raw integer states of s = 40 dimensions, M = 8, N = 65536, one thread and all threads."""
     import oracle as O
     from paper_1408_5526_gb300 import inputs
     jk = inputs.joe_kuo_table()
-    cores = min(O.max_threads(), 16)
-    out = {"cores": cores, "unit": "GNumbers/s", "sample": "s=40, M=8, N=65536 raw states"}
+    out = {"cores": threads, "unit": "GNumbers/s", "sample": "s=40, M=8, N=65536 raw states"}
     for name, seq in (("rasrap", O.RASRAP), ("sobol_ds", O.SOBOL_DS), ("philox", O.PHILOX)):
         q = O.Sequence(seq, 40, 8, SEED, joe_kuo=jk if seq == O.SOBOL_DS else None)
         row = {}
-        for th in (1, cores):
+        for th in (1, threads):
             t0 = time.perf_counter()
             a = q.stream(0, 65536, threads=th)
             row[f"recursive_{th}t"] = a.size / (time.perf_counter() - t0) / 1e9
         t0 = time.perf_counter()
-        b = q.points(65536, transform=O.RAW, threads=cores)
-        row[f"counter_based_{cores}t"] = b.size / (time.perf_counter() - t0) / 1e9
+        b = q.points(65536, transform=O.RAW, threads=threads)
+        row[f"counter_based_{threads}t"] = b.size / (time.perf_counter() - t0) / 1e9
         out[name] = row
     return out
 
@@ -417,12 +645,10 @@ def run_reference(args, rank, world):
         return
     import oracle as O
     from paper_1408_5526_gb300 import inputs
-    cores = min(O.max_threads(), 16)
+    cores = args.threads
     lm = inputs.lmm_flat(N_FWD)
     K = inputs.LMM_STRIKES
     n_sample = 8192
-    for _ in range(args.warmup):
-        pass
     t = []
     for k in range(args.steps):
         s = SEQS[k % len(SEQS)]
@@ -450,8 +676,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
-    ap.add_argument("--skip-parity", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (cpu_baseline and parity)")
     ap.add_argument("--no-extra", action="store_true", help="skip the other-configuration figures")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -466,6 +691,11 @@ def main():
             dist.init_process_group("nccl")
         else:
             dist.init_process_group("gloo")
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    args.threads = max(1, min(cores, 16))   # host threads of the oracle legs
     if args.impl == "reference":
         run_reference(args, rank, world)
     else:

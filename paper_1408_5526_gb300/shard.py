@@ -24,22 +24,31 @@ def point_range(rank: int, world: int, n_total: int) -> tuple[int, int]:
     return offset, count
 
 
-def combine_theta(theta: torch.Tensor, count: int, group=None) -> torch.Tensor:
+def combine_theta(theta: torch.Tensor, count: int, group=None, total: int | None = None) -> torch.Tensor:
     """theta_N^m over all ranks' points from this rank's theta (float64, any shape, any
     device the process group supports) over `count` points: sum_r count_r theta_r / sum_r
-    count_r.  Every rank returns the combined tensor."""
+    count_r.  Every rank returns the combined tensor.  With `total` (= sum_r count_r, known
+    on the host when the ranges come from point_range) the combination is one all-reduce of
+    theta count / total with no read-back to the host, so several estimates can be combined
+    in one call on their concatenation; without it the counts travel with the values."""
     import torch.distributed as dist
     if theta.dtype != torch.float64:
         raise TypeError("theta must be float64")
     if not (dist.is_available() and dist.is_initialized() and dist.get_world_size(group) > 1):
         return theta.clone()
+    if total is not None:
+        if total <= 0:
+            raise ValueError("no points on any rank")
+        w = theta.reshape(-1) * (float(count) / float(total))
+        dist.all_reduce(w, op=dist.ReduceOp.SUM, group=group)
+        return w.reshape(theta.shape)
     w = torch.cat([theta.reshape(-1) * float(count),
                    torch.tensor([float(count)], dtype=torch.float64, device=theta.device)])
     dist.all_reduce(w, op=dist.ReduceOp.SUM, group=group)
-    total = float(w[-1].item())
-    if total <= 0:
+    total_seen = float(w[-1].item())
+    if total_seen <= 0:
         raise ValueError("no points on any rank")
-    return (w[:-1] / total).reshape(theta.shape)
+    return (w[:-1] / total_seen).reshape(theta.shape)
 
 
 def rq_stats(theta: torch.Tensor) -> tuple[torch.Tensor, torch.Tensor]:
