@@ -47,10 +47,7 @@ __device__ __forceinline__ void batch_lmm(const BatchInst &bi, const BatchItem &
     float *wbuf = reinterpret_cast<float *>(smem_raw + o_buf) + (size_t)warp * 8 * nK * PAD;
     float *acc = reinterpret_cast<float *>(smem_raw + o_acc);
     float *cmp = acc + nw * nout;
-    for (int k = threadIdx.x; k < NF; k += blockDim.x) {
-        cst[k] = CC{md->sig[k], md->hc * md->sig[k], md->cc[k], 0.0f};
-        X0[k] = md->X0[k];
-    }
+    lmm_fill_constants<NF, float>(*md, cst, X0);
     if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md->K[threadIdx.x];
     zero_acc(acc, cmp, nw * nout);
     const LmmScal<float> sc{md->nf, md->nK, md->dl, md->inv_dl, md->disc0, md->hc, md->sqhc};

@@ -12,12 +12,17 @@
 //
 // Layout: the forwards live in registers as X_n = log(delta L_n) (base 2 in FP32).  Within
 // a step the drift is carried as W_n = h mu'_n + sqrt(h) Z (in log2 units), so one forward
-// costs ex2 + rcp + 4 FP32 ops: a = 1 / (1 + 2^-X), W += (h sigma_n) a, X += sigma_n W + cc_n.  Forward n sits in slot n-1 of an
+// costs ex2 + rcp + 4 FP32 ops: a = 1 / (1 + 2^-X), W += (h sigma_n) a, X += sigma_n W + cc_n.
+// FP32 strips of up to 40 forwards drop the + cc_n: they carry X~_n = X_n - t cc_n and read,
+// per step t and forward n, the constant g = 2^(-t cc_n) from a table, so that 1 + 2^-X =
+// 1 + g 2^-X~ is one FMA.  Two lockstep paths share one reciprocal, 1/d0 = d1 / (d0 d1) and
+// 1/d1 = d0 / (d0 d1), multiplied once by h sigma_n: per forward and pair of paths two ex2,
+// one rcp and eight FP32 operations.  Forward n sits in slot n-1 of an
 // NF-slot array (NF = 16/40/80/160).  Steps run in blocks of 8; after each block the
 // array shifts down by 8 slots, so at step tp of a block the alive slots are tp..7 of
 // group 0 (entered through an 8-way fall-through switch) plus whole groups of 8 that a
 // uniform test skips once they are dead.  The code holds NF update bodies, not NF^2/2.
-// Per-forward constants (sigma_n, h sigma_n, -sigma_n^2 h/2, in log2 units) come from
+// Per-forward constants (sigma_n, h sigma_n, -sigma_n^2 h/2 or g, in log2 units) come from
 // shared memory as one 16-byte (FP32) load shared by the thread's paths.  Payoffs are written to a padded per-warp transpose buffer and summed
 // once per block (lane r sums row r), then added to the warp's Kahan accumulator.
 #pragma once
@@ -63,11 +68,33 @@ struct LmmMath<double> {
     }
 };
 
-template <typename T>
+// FP32 strips of up to 40 forwards use the per-(step, forward) constant table (g-table).
+template <int NF, typename T>
+__host__ __device__ constexpr bool lmm_gtab() {
+    return sizeof(T) == 4 && NF <= 40;
+}
+
+// One forward of one path.  Without the g-table c = (sigma, h sigma, cc, 0) and X is the
+// log-forward; with it c = (sigma, h sigma, 2^(-t cc), 2^(t cc)) and X = X~.
+template <bool GT, typename T>
 __device__ __forceinline__ void lmm_update(T &X, const typename LmmMath<T>::C c, T &W) {
-    const T a = LmmMath<T>::rcp(T(1) + LmmMath<T>::expb(-X));   // delta L / (1 + delta L), old L
-    W = fmaT(c.y, a, W);                                         // drift through j = n
-    X = fmaT(c.x, W, X) + c.z;
+    const T e = LmmMath<T>::expb(-X);
+    const T a = LmmMath<T>::rcp(GT ? fmaT(e, c.z, T(1)) : T(1) + e);   // delta L / (1 + delta L), old L
+    W = fmaT(c.y, a, W);                                                 // drift through j = n
+    X = GT ? fmaT(c.x, W, X) : fmaT(c.x, W, X) + c.z;
+}
+
+// The same forward for two lockstep paths with one reciprocal: t = h sigma / (d0 d1), so
+// h sigma a_0 = t d1 and h sigma a_1 = t d0.
+template <bool GT, typename T>
+__device__ __forceinline__ void lmm_update2(T &X0, T &X1, const typename LmmMath<T>::C c, T &W0, T &W1) {
+    const T e0 = LmmMath<T>::expb(-X0), e1 = LmmMath<T>::expb(-X1);
+    const T d0 = GT ? fmaT(e0, c.z, T(1)) : T(1) + e0, d1 = GT ? fmaT(e1, c.z, T(1)) : T(1) + e1;
+    const T t = c.y * LmmMath<T>::rcp(d0 * d1);
+    W0 = fmaT(t, d1, W0);
+    W1 = fmaT(t, d0, W1);
+    X0 = GT ? fmaT(c.x, W0, X0) : fmaT(c.x, W0, X0) + c.z;
+    X1 = GT ? fmaT(c.x, W1, X1) : fmaT(c.x, W1, X1) + c.z;
 }
 
 template <typename T>
@@ -90,7 +117,30 @@ struct LmmScal {
     T dl, inv_dl, disc0, hc, sqhc;
 };
 
-// Shared memory: [generator stage][(sigma, cc) x NF][X0 x NF, K x 8][normals 8 x threads]
+// Constants in shared memory: with the g-table [NF + 1 steps][NF forwards], row t holding
+// (sigma_n, h sigma_n, 2^(-t cc_n), 2^(t cc_n)); otherwise [NF] of (sigma_n, h sigma_n, cc_n, 0).
+template <int NF, typename T>
+__host__ __device__ constexpr size_t lmm_cst_count() {
+    return lmm_gtab<NF, T>() ? (size_t)NF * (NF + 1) : (size_t)NF;
+}
+
+// Fill the constants and the initial state X0 (all threads of the CTA; the caller synchronises).
+template <int NF, typename T>
+__device__ __forceinline__ void lmm_fill_constants(const LmmModel<T> &md, typename LmmMath<T>::C *cst, T *X0) {
+    using CC = typename LmmMath<T>::C;
+    if constexpr (lmm_gtab<NF, T>()) {
+        for (int k = threadIdx.x; k < NF * (NF + 1); k += blockDim.x) {
+            const int t = k / NF, n = k % NF;
+            const float x = (float)t * md.cc[n];   // t cc_n in log2 units
+            cst[k] = CC{md.sig[n], md.hc * md.sig[n], exp2f(-x), exp2f(x)};
+        }
+    } else {
+        for (int k = threadIdx.x; k < NF; k += blockDim.x) cst[k] = CC{md.sig[k], md.hc * md.sig[k], md.cc[k], T(0)};
+    }
+    for (int k = threadIdx.x; k < NF; k += blockDim.x) X0[k] = md.X0[k];
+}
+
+// Shared memory: [generator stage][constants][X0 x NF, K x 8][normals 8 x threads]
 //                [transpose buffers][acc][cmp]
 template <int NF, typename T, int P = 1>
 __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, int nw, int nK, int nout,
@@ -98,7 +148,7 @@ __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, i
                                                            size_t *o_acc) {
     size_t off = stage_bytes(g);
     *o_cst = off;
-    off = align16(off + sizeof(typename LmmMath<T>::C) * NF);
+    off = align16(off + sizeof(typename LmmMath<T>::C) * lmm_cst_count<NF, T>());
     *o_x0 = off;
     off = align16(off + sizeof(T) * (NF + kMaxStrikes));
     *o_z = off;
@@ -133,6 +183,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
     using M = LmmMath<T>;
     using CC = typename M::C;
     constexpr int PAD = M::PAD;
+    constexpr bool GT = lmm_gtab<NF, T>();
     const int nf = sc.nf, nK = sc.nK;
     const T sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
     const int zs = P * blockDim.x;   // stride of one step in the normals buffer
@@ -149,7 +200,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
     const int nblk = (nf + 7) >> 3;
     for (int b = 0; b < nblk; ++b) {
         const int ngrp = (nf - 8 * b + 7) >> 3;   // groups of 8 shifted slots still alive
-        const CC *cb = cst + 8 * b;               // constants of original slot 8b + k
+        const CC *cb0 = cst + 8 * b;              // constants of original slot 8b + k (row 0)
         const int nst = min(8, nf - 8 * b);
         // phase A: the block's normals (one short generator loop)
         for (int tp = 0; tp < nst; ++tp) {
@@ -168,12 +219,24 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
             T W[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) W[p] = sqhc * zb[tp * zs + p * blockDim.x];
+            const CC *cb = GT ? cb0 + (size_t)(8 * b + tp) * NF : cb0;   // this step's row
+            // slot k of the P paths: FP32 pairs share a reciprocal, an odd path goes alone
+            auto update_slot = [&](const int k, const CC c) {
+                if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                    for (int p = 0; p + 1 < P; p += 2) lmm_update2<GT, T>(X[p][k], X[p + 1][k], c, W[p], W[p + 1]);
+                    if constexpr (P % 2 == 1) lmm_update<GT, T>(X[P - 1][k], c, W[P - 1]);
+                } else {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) lmm_update<GT, T>(X[p][k], c, W[p]);
+                }
+            };
             // group 0: alive slots tp..7, entered through a fall-through switch
             switch (tp) {
-#define RQMC_G0(k)                                                                    \
-    case (k): {                                                                       \
-        const CC c = M::lds(cb + (k));                                                \
-        _Pragma("unroll") for (int p = 0; p < P; ++p) lmm_update<T>(X[p][(k)], c, W[p]); \
+#define RQMC_G0(k)                       \
+    case (k): {                          \
+        const CC c = M::lds(cb + (k));   \
+        update_slot(k, c);               \
     }
                 RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
 #undef RQMC_G0
@@ -186,8 +249,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const CC c = M::lds(cb + 8 * gi + k);
-#pragma unroll
-                        for (int p = 0; p < P; ++p) lmm_update<T>(X[p][8 * gi + k], c, W[p]);
+                        update_slot(8 * gi + k, c);
                     }
                 }
             }
@@ -206,9 +268,11 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
                     break;
             }
             T Lf[P], dd[P];
+            // with the g-table the fixed forward's X_n = X~_n + (t+1) cc_n: one more factor 2^((t+1) cc_n)
+            const T gfix = GT ? cst[(size_t)(8 * b + tp + 1) * NF + 8 * b + tp].w : T(1);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const T e = M::expb(Xf[p]);
+                const T e = GT ? M::expb(Xf[p]) * gfix : M::expb(Xf[p]);
                 disc[p] *= M::rcp(T(1) + e);
                 Lf[p] = e * inv_dl;
                 dd[p] = active[p] ? dl * disc[p] : T(0);
@@ -274,10 +338,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     T *acc = reinterpret_cast<T *>(smem_raw + o_acc);
     T *cmp = acc + nw * nout;
     T *wacc = acc + warp * nout, *wcmp = cmp + warp * nout;
-    for (int k = threadIdx.x; k < NF; k += blockDim.x) {
-        cst[k] = CC{md.sig[k], md.hc * md.sig[k], md.cc[k], T(0)};
-        X0[k] = md.X0[k];
-    }
+    lmm_fill_constants<NF, T>(md, cst, X0);
     if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md.K[threadIdx.x];
     zero_acc(acc, cmp, nw * nout);
     const LmmScal<T> sc{md.nf, md.nK, md.dl, md.inv_dl, md.disc0, md.hc, md.sqhc};
