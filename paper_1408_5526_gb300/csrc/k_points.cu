@@ -4,6 +4,8 @@
 // ITEMS coordinates blockDim apart so every warp store is one contiguous 128-byte (FP32)
 // segment, and computes them in lockstep (shared digit / bit loop and inverse-CDF
 // polynomial).  Philox rows come four dimensions at a time from one counter.
+#include <cstring>
+
 #include "paths_common.cuh"
 
 namespace rqmc {
@@ -121,6 +123,303 @@ __global__ void __launch_bounds__(256) points_kernel(const GenParams g, uint32_t
     }
 }
 
+// ------------------------------------------------------------------ runs of consecutive points
+// Halton/Rasrap and Sobol' rows with N a multiple of 8 (and a 16-byte aligned buffer): a lane
+// owns runs of kRun = 8 consecutive points, a warp 32 runs = one chunk of 256 consecutive
+// points of a row, and a warp task kSegChunks chunks.  The lane writes its run with 16-byte
+// vector stores, so every store instruction of the warp covers consecutive bytes.
+//   Sobol': x(n) for the lane's first point once per task (bit loop), then per chunk the
+//   direction numbers of the index bits that change from n to n + 256 (the same bits in
+//   every lane when the offset is a multiple of 256), and inside a run (n a multiple of 8)
+//   x(n + k) = x(n) ^ (XOR of V_b over the bits b of k).
+//   Halton/Rasrap: Algorithm 2's odometer restated for SIMD lanes.  Write the low part of the
+//   run's first point as q p + d0; the run's points are d = d0 + k (k < 8) with q, or, past a
+//   wrap of the lowest digit, d - p with q + 1.  With the permuted digit sums of the higher
+//   digits R'(q) and R'(q + 1) computed once per run, a point costs one digit increment and
+//   one sigma lookup: R = sigma(d) p^(L-1) + R'(.).  For p >= 7 a run wraps at most once;
+//   bases 2, 3 and 5 take the direct digit expansion.
+constexpr int kRun = 8;
+constexpr int kSegChunks = 8;
+
+// sum_{k=1}^{L-1} sigma(d_k) p^(L-1-k) over the digits d_1, d_2, ... of q (least significant
+// first), in Horner order.
+__device__ __forceinline__ uint32_t halton_high(const HaltonDim &h, const uint16_t *__restrict__ sg, uint32_t q) {
+    uint32_t r = 0;
+    for (uint32_t k = 1; k < h.L; ++k) {
+        uint32_t qq = __umulhi(q, h.magic);
+        uint32_t d = q - qq * h.p;
+        if ((int32_t)d < 0) {
+            d += h.p;
+            qq -= 1;
+        }
+        r = r * h.p + (uint32_t)sg[d];
+        q = qq;
+    }
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_run(T *dst, const T (&v)[kRun]) {
+    if constexpr (sizeof(T) == 4) {
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        d4[0] = make_float4(v[0], v[1], v[2], v[3]);
+        d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+    } else {
+        ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(dst);
+#pragma unroll
+        for (int q = 0; q < kRun / 2; ++q) {
+            ulonglong2 w;
+            memcpy(&w.x, &v[2 * q], 8);
+            memcpy(&w.y, &v[2 * q + 1], 8);
+            d2[q] = w;
+        }
+    }
+}
+
+// Values of the run from raw Sobol' words.
+template <int TR, typename T>
+__device__ __forceinline__ void run_from_u32(const uint32_t (&x)[kRun], T (&v)[kRun]) {
+    if constexpr (TR == RQMC_NORMAL && sizeof(T) == 4) {
+        Unif32 u[kRun];
+        float z[kRun];
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) u[k] = unif32_from_u32(x[k]);
+        ndtri32_lockstep<kRun>(u, z);
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) v[k] = z[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) v[k] = value_from_u32<TR, T>(x[k]);
+    }
+}
+
+// One Halton row's constants as scalars: the carry-dependent fields are picked with selects,
+// so the row stays in registers (a HaltonDim indexed by the carry would live in local memory).
+struct HaltonRow {
+    unsigned long long P, S0, S1;
+    double invD;
+    uint32_t pL;
+    float inv_pL, a0, a1, b0, b1;
+    __device__ __forceinline__ explicit HaltonRow(const HaltonDim &h)
+        : P(h.P), S0(h.S[0]), S1(h.S[1]), invD(h.invD), pL(h.pL), inv_pL(h.inv_pL), a0(h.a[0]), a1(h.a[1]),
+          b0(h.b[0]), b1(h.b[1]) {}
+    __device__ __forceinline__ unsigned long long num(uint32_t R, uint32_t c) const {
+        return (unsigned long long)R * P + (c ? S1 : S0);
+    }
+    // the values of unif32_halton / unif64_halton
+    __device__ __forceinline__ bool lower(uint32_t R, uint32_t c) const {
+        const uint32_t Rc = pL - 1u - R;
+        if (R != Rc) return R < Rc;
+        const unsigned long long S = c ? S1 : S0;
+        return S <= P - 1ull - S;
+    }
+    __device__ __forceinline__ Unif32 unif32(uint32_t R, uint32_t c) const {
+        const bool lo = lower(R, c);
+        const float q = lo ? fmaf((float)R, inv_pL, c ? a1 : a0) : fmaf((float)(pL - 1u - R), inv_pL, c ? b1 : b0);
+        return Unif32{q, lo};
+    }
+    __device__ __forceinline__ Unif64 unif64(uint32_t R, uint32_t c) const {
+        const unsigned long long n = num(R, c);
+        const unsigned long long D1 = (unsigned long long)pL * P - 1ull;
+        const bool lo = n <= D1 - n;
+        return Unif64{((double)(lo ? n : D1 - n) + 0.5) * invD, lo};
+    }
+};
+
+template <int TR, typename T>
+__device__ __forceinline__ void run_from_halton(const HaltonRow &h, const uint32_t (&R)[kRun],
+                                                const uint32_t (&c)[kRun], T (&v)[kRun]) {
+    if constexpr (TR == RQMC_RAW) {
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) v[k] = (T)h.num(R[k], c[k]);
+    } else if constexpr (sizeof(T) == 4) {
+        Unif32 u[kRun];
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) u[k] = h.unif32(R[k], c[k]);
+        if constexpr (TR == RQMC_NORMAL) {
+            float z[kRun];
+            ndtri32_lockstep<kRun>(u, z);
+#pragma unroll
+            for (int k = 0; k < kRun; ++k) v[k] = z[k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < kRun; ++k) v[k] = u[k].lower ? u[k].q : 1.0f - u[k].q;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) {
+            const Unif64 w = h.unif64(R[k], c[k]);
+            v[k] = TR == RQMC_NORMAL ? ndtri64(w) : (w.lower ? w.q : 1.0 - w.q);
+        }
+    }
+}
+
+template <int TR, typename T, int SEQ>
+__global__ void __launch_bounds__(256) points_run_kernel(const GenParams g, uint32_t N, uint32_t tasks_per_row,
+                                                         unsigned long long ntasks, T *__restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const uint32_t seg_pts = 32u * kRun * kSegChunks;
+    for (unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < ntasks;
+         w += warps) {
+        const unsigned long long row = w / tasks_per_row;
+        const uint32_t seg0 = (uint32_t)(w % tasks_per_row) * seg_pts;
+        const int m = (int)(row / g.s), j = (int)(row % g.s);
+        T *dst = out + row * N;
+        if constexpr (SEQ == kSobolDS) {
+            const uint32_t *V = g.sobV + (size_t)m * g.sobV_mstride + 32 * j;
+            const uint32_t v0 = __ldg(V), v1 = __ldg(V + 1), v2 = __ldg(V + 2);
+            const uint32_t comb[kRun] = {0u, v0, v1, v0 ^ v1, v2, v2 ^ v0, v2 ^ v1, v2 ^ v1 ^ v0};
+            uint32_t n = (uint32_t)(g.offset + seg0 + kRun * lane);   // first point of the lane's run
+            uint32_t x = __ldg(g.sobShift + row);
+            for (int k = 0; k < g.sob_bits; ++k) x ^= ((n >> k) & 1u) ? __ldg(V + k) : 0u;
+            for (int c = 0; c < kSegChunks; ++c) {
+                const uint32_t i0 = seg0 + 256u * c + kRun * lane;
+                if (c > 0) {
+                    const uint32_t n2 = n + 256u;
+                    for (uint32_t d = n ^ n2; d != 0u; d &= d - 1u) x ^= __ldg(V + (__ffs(d) - 1));
+                    n = n2;
+                }
+                if (seg0 + 256u * c >= N) break;   // warp-uniform
+                uint32_t xs[kRun];
+#pragma unroll
+                for (int k = 0; k < kRun; ++k) xs[k] = x ^ comb[k];
+                T v[kRun];
+                run_from_u32<TR, T>(xs, v);
+                if (i0 < N) store_run<T>(dst + i0, v);
+            }
+        } else {
+            const HaltonDim &hg = g.hdim[row];
+            const HaltonRow hr(hg);
+            HaltonDim h;   // the digit fields only (no carry-indexed field is read from it)
+            h.p = hg.p;
+            h.L = hg.L;
+            h.pL = hg.pL;
+            h.lo0 = hg.lo0;
+            h.magic = hg.magic;
+            const uint16_t *sg = g.sigma + (size_t)m * g.sig_len + hg.sig_off;
+            const uint32_t pLm1 = h.pL / h.p;   // p^(L-1)
+            for (int c = 0; c < kSegChunks; ++c) {
+                if (seg0 + 256u * c >= N) break;   // warp-uniform
+                const uint32_t i0 = min(seg0 + 256u * c + kRun * lane, N - kRun);   // past the end: a valid run, not stored
+                uint32_t R[kRun], cc[kRun];
+                if (h.p >= 7) {
+                    uint32_t low = h.lo0 + i0;
+                    const uint32_t c0 = low >= h.pL ? 1u : 0u;
+                    low -= c0 ? h.pL : 0u;
+                    uint32_t q0 = __umulhi(low, h.magic);
+                    uint32_t d0 = low - q0 * h.p;
+                    if ((int32_t)d0 < 0) {
+                        d0 += h.p;
+                        q0 -= 1;
+                    }
+                    uint32_t q1 = q0 + 1, c1 = c0;
+                    if (q1 == pLm1) {   // the run reaches p^L: the low part wraps into the carry
+                        q1 = 0;
+                        c1 = 1;
+                    }
+                    const uint32_t R0 = halton_high(h, sg, q0), R1 = halton_high(h, sg, q1);
+#pragma unroll
+                    for (int k = 0; k < kRun; ++k) {
+                        uint32_t d = d0 + k;
+                        const bool wrap = d >= h.p;
+                        d -= wrap ? h.p : 0u;
+                        R[k] = (uint32_t)sg[d] * pLm1 + (wrap ? R1 : R0);
+                        cc[k] = wrap ? c1 : c0;
+                    }
+                } else {
+                    uint32_t ii[kRun];
+#pragma unroll
+                    for (int k = 0; k < kRun; ++k) ii[k] = i0 + k;
+                    halton_R_lockstep<kRun>(h, sg, ii, R, cc);
+                }
+                T v[kRun];
+                run_from_halton<TR, T>(hr, R, cc, v);
+                if (seg0 + 256u * c + kRun * lane < N) store_run<T>(dst + i0, v);
+            }
+        }
+    }
+}
+
+// Philox rows in runs: a warp task is (replication, block of 4 dimensions, kSegChunks chunks of
+// 256 points); a lane takes 8 consecutive points, one Philox call each gives the point's 4
+// coordinates of the block, and the lane writes each of the 4 rows' 8 values with vector stores.
+template <int TR, typename T>
+__global__ void __launch_bounds__(256) points_run_philox_kernel(const GenParams g, uint32_t N, uint32_t tasks_per_row,
+                                                                unsigned long long ntasks, T *__restrict__ out) {
+    const uint32_t lane = threadIdx.x & 31;
+    const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
+    const uint32_t seg_pts = 32u * kRun * kSegChunks;
+    const int nb = (g.s + 3) >> 2;
+    for (unsigned long long w = (unsigned long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w < ntasks;
+         w += warps) {
+        const unsigned long long rb = w / tasks_per_row;   // (m, block of 4 dimensions)
+        const uint32_t seg0 = (uint32_t)(w % tasks_per_row) * seg_pts;
+        const int m = (int)(rb / nb), jb = (int)(rb % nb);
+        for (int c = 0; c < kSegChunks; ++c) {
+            if (seg0 + 256u * c >= N) break;   // warp-uniform
+            const uint32_t i0 = seg0 + 256u * c + kRun * lane;
+            if (i0 >= N) continue;
+            uint32_t x[4][kRun];
+#pragma unroll
+            for (int k = 0; k < kRun; ++k) {
+                const unsigned long long n = g.offset + i0 + k;
+                const U32x4 r = philox4x32_10((uint32_t)n, (uint32_t)((n >> 32) & 0xFFFFu) | ((uint32_t)jb << 16),
+                                              (uint32_t)m, kTagPath | (g.inst << 8), g.key0, g.key1);
+                x[0][k] = r.x;
+                x[1][k] = r.y;
+                x[2][k] = r.z;
+                x[3][k] = r.w;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int j = 4 * jb + q;
+                if (j < g.s) {
+                    T v[kRun];
+                    run_from_u32<TR, T>(x[q], v);
+                    store_run<T>(out + ((size_t)m * g.s + j) * N + i0, v);
+                }
+            }
+        }
+    }
+}
+
+template <int TR, typename T, int SEQ>
+static cudaError_t launch_points_run(const Plan &pl, void *out, cudaStream_t st) {
+    void (*kern)(const GenParams, uint32_t, uint32_t, unsigned long long, T *);
+    if constexpr (SEQ == kPhilox) kern = points_run_philox_kernel<TR, T>;
+    else kern = points_run_kernel<TR, T, SEQ>;
+    const int threads = 256;
+    const uint32_t seg_pts = 32u * kRun * kSegChunks;
+    const uint32_t tasks_per_row = (uint32_t)((pl.N + seg_pts - 1) / seg_pts);
+    const unsigned long long rows = SEQ == kPhilox ? (unsigned long long)pl.M * ((pl.s + 3) / 4)
+                                                   : (unsigned long long)pl.M * pl.s;
+    const unsigned long long ntasks = rows * tasks_per_row;
+    int occ = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, 0);
+    if (occ < 1) occ = 1;
+    const unsigned long long blocks = (ntasks + threads / 32 - 1) / (threads / 32);
+    const unsigned grid = (unsigned)std::min<unsigned long long>(blocks, (unsigned long long)occ * sms * 4);
+    kern<<<grid, threads, 0, st>>>(pl.gen, (uint32_t)pl.N, tasks_per_row, ntasks, reinterpret_cast<T *>(out));
+    return cudaGetLastError();
+}
+
+// The run kernels apply when every run of 8 points starts on a 16-byte boundary (N a multiple
+// of 8, the buffer 16-byte aligned) and, for Sobol', the offset is a multiple of 8 (the runs'
+// index bits 0..2 are then the point's position in the run).
+static bool points_runs_apply(const Plan &pl, const void *out) {
+    return pl.N % kRun == 0 && (pl.seq == kPhilox || pl.offset % kRun == 0) && ((uintptr_t)out & 15u) == 0;
+}
+
+template <int TR, typename T>
+static cudaError_t launch_points_runs_t(const Plan &pl, void *out, cudaStream_t st) {
+    if (pl.gen.seq == kPhilox) return launch_points_run<TR, T, kPhilox>(pl, out, st);
+    return pl.gen.seq == kSobolDS ? launch_points_run<TR, T, kSobolDS>(pl, out, st)
+                                  : launch_points_run<TR, T, kRasrap>(pl, out, st);
+}
+
 template <int TR, typename T>
 static cudaError_t launch_points_t(const Plan &pl, void *out, cudaStream_t st) {
     auto kern = points_kernel<TR, T>;
@@ -141,8 +440,16 @@ static cudaError_t launch_points_t(const Plan &pl, void *out, cudaStream_t st) {
 }
 
 cudaError_t launch_points(const Plan &pl, int tr, void *out, cudaStream_t st) {
-    if (tr == RQMC_RAW) return launch_points_t<RQMC_RAW, unsigned long long>(pl, out, st);
     const bool f32 = pl.prec == RQMC_FP32;
+    if (points_runs_apply(pl, out)) {
+        if (tr == RQMC_RAW) return launch_points_runs_t<RQMC_RAW, unsigned long long>(pl, out, st);
+        if (tr == RQMC_UNIFORM)
+            return f32 ? launch_points_runs_t<RQMC_UNIFORM, float>(pl, out, st)
+                       : launch_points_runs_t<RQMC_UNIFORM, double>(pl, out, st);
+        return f32 ? launch_points_runs_t<RQMC_NORMAL, float>(pl, out, st)
+                   : launch_points_runs_t<RQMC_NORMAL, double>(pl, out, st);
+    }
+    if (tr == RQMC_RAW) return launch_points_t<RQMC_RAW, unsigned long long>(pl, out, st);
     if (tr == RQMC_UNIFORM)
         return f32 ? launch_points_t<RQMC_UNIFORM, float>(pl, out, st) : launch_points_t<RQMC_UNIFORM, double>(pl, out, st);
     return f32 ? launch_points_t<RQMC_NORMAL, float>(pl, out, st) : launch_points_t<RQMC_NORMAL, double>(pl, out, st);

@@ -5,7 +5,8 @@ word): ranges near 2^40 that cross a 2^32 boundary, and the last points below 2^
 Sobol' indices are 32-bit: the last N points below 2^32.  Halton/Rasrap split the index at
 digit L with p^L <= 2^31 for every base (the low part lo0 + i stays below 2^32): runs at
 exactly the largest N this allows for s = 1 (N = 2^31), s = 2 (N = 3^19) and s = 360
-(N = 1291^2), checked on windows at the start, the end and inside the range.  One more
+(N = 1291^2, and one point less, a multiple of 8 that the run kernel takes), checked on
+windows at the start, the end and inside the range.  One more
 point than each limit is refused before any launch.  The caplet kernel's own generator (a
 separate code path from the point stream) runs at the same large offsets."""
 import numpy as np
@@ -30,9 +31,10 @@ def _raw(t):
     return t.cpu().numpy().view(np.uint64)
 
 
-@pytest.mark.parametrize("offset", [(1 << 40) + (1 << 32) - 1500, (1 << 48) - 3001])
-def test_philox_points_at_large_offsets(R, offset):
-    N, M, s = 3001, 2, 10
+@pytest.mark.parametrize("offset,N", [((1 << 40) + (1 << 32) - 1500, 3001), ((1 << 40) + (1 << 32) - 1500, 3000),
+                                      ((1 << 48) - 3001, 3001), ((1 << 48) - 3000, 3000)])
+def test_philox_points_at_large_offsets(R, offset, N):
+    M, s = 2, 10
     gpu = _raw(R.rqmc_points(s, N, M, O.PHILOX, 7, offset=offset, transform="raw"))
     ora = O.Sequence(O.PHILOX, s, M, 7).points(N, offset, transform=O.RAW)
     assert np.array_equal(gpu, ora)
@@ -45,8 +47,9 @@ def test_philox_refuses_beyond_48_bits(R):
 
 
 @pytest.mark.parametrize("seq", [O.SOBOL_DS, O.SOBOL_LMS])
-def test_sobol_points_up_to_two_to_the_32(R, seq):
-    N, M, s = 3001, 2, 40
+@pytest.mark.parametrize("N", [3001, 3000])
+def test_sobol_points_up_to_two_to_the_32(R, seq, N):
+    M, s = 2, 40
     offset = (1 << 32) - N
     gpu = _raw(R.rqmc_points(s, N, M, seq, 7, offset=offset, transform="raw"))
     ora = O.Sequence(seq, s, M, 7, joe_kuo=JK).points(N, offset, transform=O.RAW)
@@ -60,7 +63,7 @@ def _windows(N):
 
 
 @pytest.mark.parametrize("seq,s,N", [(O.RASRAP, 1, 1 << 31), (O.HALTON_RS, 2, 3 ** 19), (O.RASRAP, 2, 3 ** 19),
-                                     (O.RASRAP, 360, 1291 ** 2)])
+                                     (O.RASRAP, 360, 1291 ** 2), (O.RASRAP, 360, 1291 ** 2 - 1)])
 def test_halton_at_the_digit_split_limit(R, seq, s, N):
     import torch
     M = 1
@@ -74,8 +77,9 @@ def test_halton_at_the_digit_split_limit(R, seq, s, N):
     p.close()
     del out
     torch.cuda.empty_cache()
-    with pytest.raises(R.RqmcError):
-        R.Plan.points(s, N + 1, M, seq, 5, transform="raw")
+    if N in (1 << 31, 3 ** 19, 1291 ** 2):   # the largest N of its s: one more point is refused
+        with pytest.raises(R.RqmcError):
+            R.Plan.points(s, N + 1, M, seq, 5, transform="raw")
 
 
 @pytest.mark.parametrize("seq,offset", [(O.PHILOX, (1 << 40) + (1 << 32) - 1500), (O.PHILOX, (1 << 48) - 3001),

@@ -32,9 +32,11 @@ def _to_np(t):
 @pytest.mark.parametrize("seq,s", [(O.HALTON_RS, 8), (O.RASRAP, 8), (O.RASRAP, 360), (O.SOBOL_DS, 40),
                                    (O.SOBOL_LMS, 40), (O.SOBOL_LMS, 360),
                                    (O.SOBOL_DS, 360), (O.PHILOX, 10)])
-@pytest.mark.parametrize("offset", [0, 12345])
-def test_points_raw_bit_exact(R, seq, s, offset):
-    N, M = 3001, 3
+@pytest.mark.parametrize("offset,N", [(0, 3001), (12345, 3001), (0, 3000), (12344, 4096)])
+def test_points_raw_bit_exact(R, seq, s, offset, N):
+    """N and the offset multiples of 8 take the run kernel (runs of 8 consecutive points per
+    lane, vector stores), the others the per-point kernel."""
+    M = 3
     gpu = _to_np(R.rqmc_points(s, N, M, seq, 7, offset=offset, transform="raw"))
     ora = O.Sequence(seq, s, M, 7, joe_kuo=JK).points(N, offset, transform=O.RAW)
     assert gpu.shape == ora.shape
@@ -57,8 +59,9 @@ def test_points_plan_matches_one_shot(R, seq, prec, transform):
 
 
 @pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
-def test_points_fp64_uniform_and_normal(R, seq):
-    N, M, s = 2500, 2, 16
+@pytest.mark.parametrize("N", [2500, 2504])
+def test_points_fp64_uniform_and_normal(R, seq, N):
+    M, s = 2, 16
     q = O.Sequence(seq, s, M, 11, joe_kuo=JK)
     u = _to_np(R.rqmc_points(s, N, M, seq, 11, prec="fp64", transform="uniform"))
     np.testing.assert_allclose(u, q.points(N, transform=O.UNIFORM), rtol=0, atol=4e-16)
@@ -68,8 +71,9 @@ def test_points_fp64_uniform_and_normal(R, seq):
 
 
 @pytest.mark.parametrize("seq", [O.HALTON_RS, O.RASRAP, O.SOBOL_DS, O.PHILOX, O.SOBOL_LMS])
-def test_points_fp32_uniform_and_normal(R, seq):
-    N, M, s = 2500, 2, 40
+@pytest.mark.parametrize("N", [2500, 2504])
+def test_points_fp32_uniform_and_normal(R, seq, N):
+    M, s = 2, 40
     q = O.Sequence(seq, s, M, 13, joe_kuo=JK)
     u = _to_np(R.rqmc_points(s, N, M, seq, 13, prec="fp32", transform="uniform"))
     uo = q.points(N, transform=O.UNIFORM)
