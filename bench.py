@@ -87,13 +87,14 @@ def mbs_algorithmic_ops(months, paths):
 
 def adjoint_algorithmic_ops(nf, d, paths):
     """Pathwise adjoint of a d-factor strip, per path: the forward sweep's nf(nf+1)/2 forward
-    updates (ex2 + rcp, 2 + 3d FP32) and the fixings' ex2 + rcp in both sweeps, the reverse
-    sweep's as many adjoint updates (3 + 7d FP32), and 2 nf d inverse CDFs (the normals drawn
-    in the forward sweep and regenerated in the reverse one, lg2 + 17 FP32 each).  SFU slots
-    and FP32 operations."""
+    updates (ex2 + rcp, 2 + 3d FP32), the reverse sweep's as many steps back (the pre-step state
+    reconstructed from the post-step one, 2 + d FP32, and its drift factor again, ex2 + rcp)
+    with their adjoint updates (3 + 7d FP32), the fixings' ex2 + rcp in both sweeps, and 2 nf d
+    inverse CDFs (the normals drawn in the forward sweep and regenerated in the reverse one,
+    lg2 + 17 FP32 each).  SFU slots and FP32 operations."""
     upd = nf * (nf + 1) // 2
-    slots = 1.5 * (upd + 2 * nf) + 2 * nf * d
-    fma = (2 + 3 * d) * upd + (3 + 7 * d) * upd + 2 * nf * d * 17
+    slots = 1.5 * (2 * upd + 2 * nf) + 2 * nf * d
+    fma = (2 + 3 * d) * upd + (2 + d) * upd + (3 + 7 * d) * upd + 2 * nf * d * 17
     return slots * paths, fma * paths
 
 

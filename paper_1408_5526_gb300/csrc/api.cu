@@ -575,21 +575,20 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
     if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
     pl->grid = adjoint_grid(*pl);
     if (pl->grid < 1) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
-    // per-thread records (float4 units): per step t a header and chunks t/4 .. ceil(nf/4)-1
-    size_t E = 0;
-    for (int t = 0; t < nf; ++t) E += 4 * (size_t)(1 + (nf + 3) / 4 - t / 4);
-    // column stride: the grid's threads plus 96 unused columns, so consecutive record rows are
-    // not 64 KiB-aligned multiples of each other (fewer DRAM partition conflicts)
-    const uint32_t T = (uint32_t)pl->grid * (uint32_t)pl->threads + 96;
+    // per-thread columns (stride T): records, one float2 per step (the step's prefix total A);
+    // adjoints Xb, NF/4 float4 chunks; then the accumulators
+    const uint32_t T = (uint32_t)pl->grid * (uint32_t)pl->threads + 96;   // + 96: rows not 64 KiB-periodic
+    const size_t rec_floats = 2 * (size_t)nf, xb_floats = (size_t)pl->nf_bucket;
     const size_t rows = 1 + 2 * (size_t)pl->nf_bucket + (size_t)nf * n_strikes;   // vega chunks, value, delta, prices
     pl->adjs.T = T;
-    const size_t bytes = sizeof(float) * ((size_t)E + rows) * T;
+    const size_t bytes = sizeof(float) * (rec_floats + xb_floats + rows) * T;
     void *buf = nullptr;
     cudaError_t e = cudaMalloc(&buf, bytes);
     if (e != cudaSuccess) { destroy(pl, 0); set_error("adjoint: scratch allocation failed"); return RQMC_ENOMEM; }
     pl->adj_buf = buf;
     pl->adjs.store = static_cast<float *>(buf);
-    pl->adjs.acc = static_cast<float *>(buf) + (size_t)E * T;
+    pl->adjs.xb = static_cast<float *>(buf) + rec_floats * T;
+    pl->adjs.acc = pl->adjs.xb + xb_floats * T;
     if ((e = cudaMemset(pl->adjs.acc, 0, sizeof(float) * rows * T)) != cudaSuccess) {
         destroy(pl, 0);
         return cuda_fail(e, "adjoint scratch clear");

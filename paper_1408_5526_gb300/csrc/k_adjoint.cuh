@@ -7,25 +7,26 @@
 //     a_n = 1 / (1 + 2^-X_n)               (= delta L_n / (1 + delta L_n))
 //     A_n = sum_{j<=n, alive} sigma_j a_j   (d-vector prefix)
 //     X_n += log2 e (h sigma_n.A_n + sqrt(h) sigma_n.Z - h |sigma_n|^2 / 2).
-// Each thread keeps its path's X_n (then the adjoints) in a shared-memory column with a
-// compile-time stride and loops over the alive forwards four slots (one chunk) at a time.
-// The forward sweep stores, per step, a header (the pre-step X of the forward fixed at that
-// step, the step's prefix total A) and the a_n in 16-byte chunks aligned to absolute forward
-// slots, interleaved by thread in global scratch: one coalesced 128-bit streaming store per
-// four forwards, read back once by the reverse sweep (prefetched into L2 one step ahead, then
-// into registers two chunks ahead).  The vega accumulators
-// use the same chunking and are updated by vector reductions that the thread does not wait
-// for.  With Xb_n = dV/dX_n and B_n = sum_{m>=n} Xb_m sigma_m, the reverse sweep of a step
-// visits the alive slots top-down and applies
+// Each thread keeps its path's X_n in a shared-memory column with a compile-time stride and
+// loops over the alive forwards four slots (one chunk) at a time.  The forward sweep stores
+// one record per step: the step's prefix total A (d floats).  The reverse sweep walks the
+// alive slots of a step top-down and RECONSTRUCTS the pre-step state from the post-step one:
+// with E = h A_n + sqrt(h) Z running down from the stored total (E -= h sigma_n a_n past
+// slot n), the step's increment of slot n is log2 e sigma_n.E - h |sigma_n|^2 log2 e / 2, so
+//     X_n(t) = X_n(t+1) - (log2 e sigma_n.E + cc_n),   a_n = 1 / (1 + 2^-X_n(t)),
+// and the shared-memory column walks back from X(T) to X(0) (rounding moves it by about one
+// ulp per step).  With Xb_n = dV/dX_n and B_n = sum_{m>=n} Xb_m sigma_m, the reverse step
+// applies, top-down,
 //     sigma_bar_n = log2 e [Xb_n (h A_n + sqrt(h) Z - h sigma_n) + h a_n B_n]
 //     Xb_n       += h (sigma_n.B_n) a_n (1 - a_n)
-// (A_n recovered top-down from the stored total), and at the fixing of forward n (Y = its
-// post-step X, L = 2^Y / delta, G_n = sum_{m>=n} P_m)
+// and at the fixing of forward n (Y = its post-step X, L = 2^Y / delta, G_n = sum_{m>=n} P_m)
 //     Xb_n       += ln 2 [sum_k w_{n,k} delta 1{L > K_k} D_n L - a(Y) G_n].
-// The normals of a step are regenerated from the counter, never stored.  At the end
-// dV/dL_n(0) = Xb_n / (L_n(0) ln 2) and dV/dvol_n = sum over steps of sigma_bar_n . b_n.
-// Per-thread value / delta / vega / price accumulators sit in global columns; each
-// (replication, tile) unit sums its CTA's columns in double into its own partial row.
+// The adjoints Xb live in per-thread global columns (16-byte chunks, loaded two chunks ahead;
+// the columns stay in L2), the vega accumulators likewise, updated by vector reductions that
+// the thread does not wait for.  The normals of a step are regenerated from the counter, never
+// stored.  At the end dV/dL_n(0) = Xb_n / (L_n(0) ln 2) and dV/dvol_n = sum over steps of
+// sigma_bar_n . b_n.  Per-thread value / delta / vega / price accumulators sit in global
+// columns; each (replication, tile) unit sums its CTA's columns in double into its own row.
 #pragma once
 #include "paths_common.cuh"
 
@@ -46,12 +47,8 @@ constexpr int kAdjThreads = kAdjointThreads;
 
 // Shared memory: [generator stage][forward constants (sigma_1, sigma_2, cc, 0) x NF]
 //                [reverse constants (h sigma_1, h sigma_2, b_1 log2 e, b_2 log2 e) x NF]
-//                [per-thread state x NF x kAdjThreads]  (forward X, then the adjoints Xb)
-// L2 prefetch: no register is written, so the thread does not wait for it.
-__device__ __forceinline__ void prefetch_l2(const void *p) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
+//                [reconstruction constants (sigma_1 log2 e, sigma_2 log2 e, cc, 0) x NF]
+//                [per-thread state x NF x kAdjThreads]  (X)
 template <int NF>
 __host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, size_t *o_fw, size_t *o_rv,
                                                            size_t *o_st) {
@@ -59,7 +56,7 @@ __host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, s
     *o_fw = off;
     off += sizeof(float4) * NF;
     *o_rv = off;
-    off += sizeof(float4) * NF;
+    off += sizeof(float4) * 2 * NF;
     *o_st = off;
     off = align16(off + sizeof(float) * NF * (size_t)kAdjThreads);
     return off;
@@ -81,17 +78,21 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
     adj_smem_layout<NF>(g, &o_fw, &o_rv, &o_st);
     float4 *cfw = reinterpret_cast<float4 *>(smem_raw + o_fw);
     float4 *crv = reinterpret_cast<float4 *>(smem_raw + o_rv);
+    float4 *crc = crv + NF;
     float *xcol = reinterpret_cast<float *>(smem_raw + o_st) + threadIdx.x;   // slot n at xcol[n BD]
     const float l2e = 1.4426950408889634f, ln2 = 0.6931471805599453f;
     for (int k = threadIdx.x; k < NF; k += BD) {
         cfw[k] = make_float4(md.sg[k][0], md.sg[k][1], md.cc[k], 0.0f);
         crv[k] = make_float4(md.h * md.sg[k][0], md.h * md.sg[k][1], md.b[k][0] * l2e, md.b[k][1] * l2e);
+        crc[k] = make_float4(md.sg[k][0] * l2e, md.sg[k][1] * l2e, md.cc[k], 0.0f);
     }
     const uint32_t T = sc.T;                              // threads in the grid: column stride
     const uint32_t gt = blockIdx.x * BD + threadIdx.x;
     // accumulators: vega as float4 chunks [NF/4][T], then value [T], delta [NF][T], prices [nf nK][T]
     float4 *const vega4 = reinterpret_cast<float4 *>(sc.acc) + gt;
     float *accs = sc.acc + (size_t)NF * T + gt;
+    float4 *const xb4 = reinterpret_cast<float4 *>(sc.xb) + gt;   // adjoints Xb as float4 chunks [NF/4][T]
+    float2 *const rec = reinterpret_cast<float2 *>(sc.store) + gt; // per step t: prefix total A at rec[t T]
     const int nf = md.nf, nK = md.nK, nch = (nf + 3) >> 2;
     const float h = md.h, inv_h = 1.0f / md.h, hl = md.h * l2e, sqhl = md.sqh * l2e, dl = md.dl, inv_dl = md.inv_dl;
     uint32_t u0, u1;
@@ -116,10 +117,6 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
             // slots nf .. 4 nch - 1 are padding with zero volatility: they stay constant and feed
             // nothing into the drifts, the adjoints or the vegas, so full chunks need no checks
             for (int n = 0; n < 4 * nch; ++n) xcol[n * BD] = md.X0[n];
-            // records, in float4 units: per step a header (X of the fixed forward, the step's
-            // prefix total A) and the a_n of chunks t/4 .. nch-1 (absolute slots, dead slots 0).
-            // Each record is read once, by the reverse sweep: streaming (evict-first) accesses.
-            float4 *rec = reinterpret_cast<float4 *>(sc.store) + gt;
             // ---------------- forward sweep
             float disc = md.disc0, value = 0.0f;
             for (int t = 0; t < nf; ++t) {
@@ -132,11 +129,8 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                 } else {
                     Az0 = sqhl * Draw<float>::normal(pg, t);
                 }
-                const float Xpre = xcol[t * BD];
-                float4 *hdr = rec;
-                rec += T;
-                // one chunk of four slots; slots below jlo are fixed forwards (a = 0).  All loads
-                // come before the stores, so the four exponentials overlap.
+                // one chunk of four slots; slots below jlo are fixed forwards.  All loads come
+                // before the stores, so the four exponentials overlap.
                 auto fwd_chunk = [&](int c, int jlo) {
                     float *px = xcol + c * (4 * BD);
                     const float4 *pc = cfw + 4 * c;
@@ -161,12 +155,10 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                             px[j * BD] = X[j] + inc;
                         }
                     }
-                    __stcs(rec, make_float4(a[0], a[1], a[2], a[3]));
-                    rec += T;
                 };
                 fwd_chunk(t >> 2, t & 3);
                 for (int c = (t >> 2) + 1; c < nch; ++c) fwd_chunk(c, 0);
-                __stcs(hdr, make_float4(Xpre, A0, A1, 0.0f));
+                rec[(size_t)t * T] = make_float2(A0, A1);
                 const float e = ex2_approx(xcol[t * BD]);
                 disc *= rcp_approx(1.0f + e);
                 const float L = e * inv_dl;
@@ -180,38 +172,27 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                 }
                 value += pn;
             }
-            // ---------------- reverse sweep (xcol now holds the adjoints Xb); skipped for zero weights
-            for (int n = 0; n < 4 * nch; ++n) xcol[n * BD] = 0.0f;
+            // ---------------- reverse sweep (skipped for zero weights): xcol walks back to X(0),
+            // the adjoints accumulate in the thread's global columns
+            for (int c = 0; c < nch; ++c) xb4[(size_t)c * T] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float Dcur = disc, G = 0.0f;
             for (int t = md.reverse ? nf - 1 : -1; t >= 0; --t) {
-                const int c0 = t >> 2;
-                rec -= (size_t)(1 + nch - c0) * T;
-                if (t > 0) {   // the previous step's records into L2, a whole step ahead
-                    const int c0p = (t - 1) >> 2;
-                    const float4 *pv = rec - (size_t)(1 + nch - c0p) * T;
-                    for (int k = 0; k <= nch - c0p; ++k) prefetch_l2(pv + (size_t)k * T);
-                }
-                const float4 h4 = __ldcs(rec);
-                const float4 ac = __ldcs(rec + T);              // chunk c0
-                // software pipeline over the chunks nch-1 .. c0, loaded two ahead
-                const float4 *q = rec + (size_t)(nch - c0) * T;  // chunk nch-1
-                float4 p0 = __ldcs(q);
+                const int c0 = t >> 2, jt = t & 3;
+                const float2 At = rec[(size_t)t * T];
+                // software pipeline over the adjoint chunks nch-1 .. c0, loaded two ahead
+                const float4 *q = xb4 + (size_t)(nch - 1) * T;
+                float4 p0 = *q;
                 q -= T;
                 float4 p1 = p0;
                 if (nch - 2 >= c0) {
-                    p1 = __ldcs(q);
+                    p1 = *q;
                     q -= T;
                 }
                 float Z0, Z1 = 0.0f;
                 if constexpr (D == 2) normals32_two_dims<SEQ>(pg, 2 * t, 2 * t + 1, Z0, Z1);
                 else Z0 = Draw<float>::normal(pg, t);
-                // post-step value of the fixed forward, with the forward sweep's operations
-                const float4 ct = cfw[t];
-                const int jt = t & 3;
-                const float a0 = jt == 0 ? ac.x : jt == 1 ? ac.y : jt == 2 ? ac.z : ac.w;
-                float inc = fmaf(ct.x, fmaf(fmaf(ct.x, a0, 0.0f), hl, sqhl * Z0), ct.z);
-                if constexpr (D == 2) inc = fmaf(ct.y, fmaf(fmaf(ct.y, a0, 0.0f), hl, sqhl * Z1), inc);
-                const float Y = h4.x + inc;
+                // the fixed forward's post-step value is the column's current value
+                const float Y = xcol[t * BD];
                 const float e = ex2_approx(Y);
                 const float aY = e * rcp_approx(1.0f + e);
                 const float L = e * inv_dl;
@@ -225,31 +206,37 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                 }
                 G = fmaf(pn * dl, Dcur, G);
                 // an inactive lane (past N) follows a dummy path with zero adjoint source
-                xcol[t * BD] += active ? ln2 * (dpn * dl * Dcur * L - aY * G) : 0.0f;
+                const float src = active ? ln2 * (dpn * dl * Dcur * L - aY * G) : 0.0f;
                 Dcur *= 1.0f + e;                             // D_{n-1} = D_n (1 + delta L_n)
                 // top-down over the alive slots n: E = h A_n + sqrt(h) Z (A_n the step's prefix
                 // sum through n) and hB = h B_n = h sum_{m>=n} Xb_m sigma_m, per factor; the
                 // update of Xb_n is h (sigma.B) a (1 - a) = (h sigma . hB) a (1 - a) / h
-                float E0 = fmaf(h, h4.y, md.sqh * Z0), E1 = fmaf(h, h4.z, md.sqh * Z1);
+                float E0 = fmaf(h, At.x, md.sqh * Z0), E1 = fmaf(h, At.y, md.sqh * Z1);
                 float hB0 = 0.0f, hB1 = 0.0f;
                 float4 *vg = vega4 + (size_t)(nch - 1) * T;
-                auto rev_chunk = [&](int c, int jlo, const float4 a4) {
+                auto rev_chunk = [&](int c, int jlo, float4 xb) {
                     float *px = xcol + c * (4 * BD);
                     const float4 *pc = crv + 4 * c;
-                    const float aa[4] = {a4.x, a4.y, a4.z, a4.w};
-                    float Xb[4], vv[4];
-                    float4 cn[4];
+                    const float4 *pq = crc + 4 * c;
+                    float Xb[4] = {xb.x, xb.y, xb.z, xb.w}, vv[4], Xp[4];
+                    float4 cn[4], cr[4];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        Xb[j] = px[j * BD];
+                        Xp[j] = px[j * BD];
                         cn[j] = pc[j];
+                        cr[j] = pq[j];
                     }
 #pragma unroll
                     for (int j = 3; j >= 0; --j) {
                         vv[j] = 0.0f;
                         if (j >= jlo) {
+                            // pre-step state of slot n and its drift factor a_n
+                            float inc = fmaf(cr[j].x, E0, cr[j].z);
+                            if constexpr (D == 2) inc = fmaf(cr[j].y, E1, inc);
+                            const float Xn = Xp[j] - inc;
+                            const float a = rcp_approx(1.0f + ex2_approx(-Xn));
+                            px[j * BD] = Xn;
                             // sigma_bar = Xb (h (A_n - sigma_n) + sqrt(h) Z) + h a_n B_n, per factor
-                            const float a = aa[j];
                             hB0 = fmaf(Xb[j], cn[j].x, hB0);
                             float S = cn[j].x * hB0;              // h^2 sigma.B
                             float v = cn[j].z * fmaf(Xb[j], E0 - cn[j].x, a * hB0);
@@ -261,26 +248,40 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                                 E1 = fmaf(-cn[j].y, a, E1);
                             }
                             vv[j] = v;
-                            px[j * BD] = fmaf(S, inv_h * fmaf(-a, a, a), Xb[j]);   // + h (sigma.B) a (1 - a)
+                            Xb[j] = fmaf(S, inv_h * fmaf(-a, a, a), Xb[j]);   // + h (sigma.B) a (1 - a)
                         }
                     }
+                    xb4[(size_t)c * T] = make_float4(Xb[0], Xb[1], Xb[2], Xb[3]);
                     red_add_v4(vg, vv);
                     vg -= T;
                 };
                 for (int c = nch - 1; c > c0; --c) {
-                    const float4 a4 = p0;
+                    const float4 xb = p0;
                     p0 = p1;
                     if (c - 2 >= c0) {
-                        p1 = __ldcs(q);
+                        p1 = *q;
                         q -= T;
                     }
-                    rev_chunk(c, 0, a4);
+                    rev_chunk(c, 0, xb);
                 }
+                // the fixing's source enters the fixed forward's adjoint before its chunk
+                p0.x += jt == 0 ? src : 0.0f;
+                p0.y += jt == 1 ? src : 0.0f;
+                p0.z += jt == 2 ? src : 0.0f;
+                p0.w += jt == 3 ? src : 0.0f;
                 rev_chunk(c0, jt, p0);
             }
             if (active) {
                 atomicAdd(accs, value);
-                for (int n = 0; n < nf; ++n) atomicAdd(accs + (size_t)(1 + n) * T, xcol[n * BD] * md.invL0ln2[n]);
+                for (int c = 0; c < nch; ++c) {
+                    const float4 xb = xb4[(size_t)c * T];
+                    const float xs[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int n = 4 * c + j;
+                        if (n < nf) atomicAdd(accs + (size_t)(1 + n) * T, xs[j] * md.invL0ln2[n]);
+                    }
+                }
             }
         }
         // ---------------- unit flush: sum the CTA's columns in double

@@ -89,7 +89,8 @@ struct AdjModel {
 
 // Per-thread global columns of the adjoint kernel (column stride T = threads in the grid).
 struct AdjScratch {
-    float *store;   // forward-sweep records, float4 chunks interleaved by thread
+    float *store;   // forward-sweep records: per step the prefix total A as float2 [nf][T]
+    float *xb;      // adjoints dV/dX_n as float4 chunks [NF/4][T]
     float *acc;     // vega as float4 chunks [NF/4][T], then value, dV/dL_n(0) [NF], caplet prices [nf nK]
     uint32_t T;
 };
