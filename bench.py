@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one lmm_caplet_kernel<40, 1, float> launch
 # (Rasrap) of this workload, from an ncu capture of the kernel as committed; None whenever
 # that kernel has changed since the capture.
-LMM_TRAFFIC_BYTES = None
+LMM_TRAFFIC_BYTES = 711.7e3
 
 
 def _peaks():
@@ -402,219 +402,233 @@ def other_workloads(args, dev, seed, pk):
     T = args.threads
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     out = {}
+    chosen = set(args.extra.split(",")) if args.extra != "all" else None
 
-    # ---- product integrand, s = 8, N = 4096, M = 32, random-start Halton, FP64
-    s, N, M = 8, 4096, 32
-    a = inputs.product_weights(s)
-    p = rqmc.Plan.product(s, N, M, "halton_rs", seed, a, prec="fp64")
-    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
-    ms = _time_plan(lambda: p.execute(o), 10, flush)
-    th = o.cpu().numpy()
-    p.close()
-    th_o, t_o = _timed_oracle(lambda: O.product_theta(O.Sequence(O.HALTON_RS, s, M, seed), N, a, threads=T))
-    rel = float(np.max(np.abs(th - th_o) / np.abs(th_o)))
-    out["product_s8_N4096_M32_fp64"] = {
-        "ms": ms, "path_steps_per_s": s * N * M / (ms / 1e3), "rq": float(th.mean()), "exact": 1.0,
-        "parity": {"ok": rel <= 1e-11, "tol": 1e-11, "max_rel_err": rel, "checked": "all 32 replications"},
-        "cpu_baseline": {"value": s * N * M / t_o, "unit": "point-dims/s", "cores": T, "kind": "oracle",
-                         "sample": "the whole workload"},
-        "roofline": {"bound": "latency", "note": "one launch of 1M point-dims plus the theta reduction; at "
-                     f"{ms * 1e3:.0f} us the launch and tail dominate", "frac": None}}
+    def want(name):
+        return chosen is None or name in chosen
 
-    # ---- LMM caplets in FP64 (same 40-forward workload), Rasrap
     lm = inputs.lmm_flat(N_FWD)
     K = inputs.LMM_STRIKES
-    p = rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, "rasrap", seed, prec="fp64")
-    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
-    ms = _time_plan(lambda: p.execute(o), 2, flush)
-    th = o.cpu().numpy().reshape(M_REPL, -1)
-    p.close()
-    mr = 4
-    th_o, t_o = _timed_oracle(lambda: O.lmm_caplets(O.Sequence(O.RASRAP, N_FWD, M_REPL, seed), lm, K, N_PATHS,
-                                                    m_range=(0, mr), threads=T))
-    rel = float(np.max(np.abs(th[:mr] - th_o) / np.abs(th_o)))
-    pairs = lmm_fp64_pairs(N_FWD, N_PATHS * M_REPL)
-    out["lmm_caplets_40_N65536_M64_fp64_rasrap"] = {
-        "ms": ms, "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3),
-        "parity": {"ok": rel <= 1e-11, "tol": 1e-11, "max_rel_err": rel, "checked": f"replications 0..{mr - 1}, full N"},
-        "cpu_baseline": {"value": mr * N_PATHS * N_FWD / t_o, "unit": "path-steps/s", "cores": min(T, mr),
-                         "kind": "oracle", "sample": f"{mr} replications x N={N_PATHS}"},
-        "roofline": {"bound": "fp64", "pipe": "fp64 update pair (exp + reciprocal)",
-                     "achieved": round(pairs / (ms / 1e3) / 1e9, 3), "peak": round(pk.fp64_pair / 1e9, 3),
-                     "unit": "G FP64 update pairs/s", "frac": round(pairs / (ms / 1e3) / pk.fp64_pair, 4),
-                     "peak_source": f"probed: {pk.probe['fp64_pair']:.3f} pairs per SM per clock x {pk.sms} SMs x "
-                                    f"{pk.mhz:.0f} MHz"}}
-
-    # ---- MBS, 360 months, N = 65536, M = 64, FP32 + Kahan
-    mb = inputs.mbs_paper(360)
-    res = {}
     ids = {"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX}
-    for s_ in SEQS:
-        p = rqmc.Plan.mbs(mb, N_PATHS, M_REPL, s_, seed, prec="fp32")
+
+    # ---- product integrand, s = 8, N = 4096, M = 32, random-start Halton, FP64
+    if want("product"):
+        s, N, M = 8, 4096, 32
+        a = inputs.product_weights(s)
+        p = rqmc.Plan.product(s, N, M, "halton_rs", seed, a, prec="fp64")
         o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
-        ms = _time_plan(lambda: p.execute(o), 3, flush)
+        ms = _time_plan(lambda: p.execute(o), 10, flush)
         th = o.cpu().numpy()
         p.close()
-        q = O.Sequence(ids[s_], 360, M_REPL, seed, joe_kuo=jk)
-        th_o, t_o = _timed_oracle(lambda: _oracle_points(
-            lambda off, n: O.mbs_theta(q, mb, n, offset=off, m_range=(0, 1), threads=1), N_PATHS, T))
-        rel = float(abs(th[0] - th_o[0]) / abs(th_o[0]))
-        slots, fma = mbs_algorithmic_ops(360, N_PATHS * M_REPL)
-        res[s_] = {"ms": ms, "path_steps_per_s": N_PATHS * M_REPL * 360 / (ms / 1e3), "rq": float(th.mean()),
-                   "parity": {"ok": rel <= 1e-4, "tol": 1e-4, "max_rel_err": rel,
-                              "checked": "replication 0 at full N"},
-                   "cpu_baseline": {"value": N_PATHS * 360 / t_o, "unit": "path-steps/s", "cores": T,
-                                    "kind": "oracle", "sample": f"replication 0 x N={N_PATHS} (point ranges)"},
-                   "roofline": pk.alu(slots, fma, ms / 1e3, f"mbs_kernel<float,{s_}>")}
-    out["mbs_360_N65536_M64_fp32"] = res
+        th_o, t_o = _timed_oracle(lambda: O.product_theta(O.Sequence(O.HALTON_RS, s, M, seed), N, a, threads=T))
+        rel = float(np.max(np.abs(th - th_o) / np.abs(th_o)))
+        out["product_s8_N4096_M32_fp64"] = {
+            "ms": ms, "path_steps_per_s": s * N * M / (ms / 1e3), "rq": float(th.mean()), "exact": 1.0,
+            "parity": {"ok": rel <= 1e-11, "tol": 1e-11, "max_rel_err": rel, "checked": "all 32 replications"},
+            "cpu_baseline": {"value": s * N * M / t_o, "unit": "point-dims/s", "cores": T, "kind": "oracle",
+                             "sample": "the whole workload"},
+            "roofline": {"bound": "latency", "note": "one launch of 1M point-dims plus the theta reduction; at "
+                         f"{ms * 1e3:.0f} us the launch and tail dominate", "frac": None}}
+
+    # ---- LMM caplets in FP64 (same 40-forward workload), Rasrap
+    if want("fp64"):
+        p = rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, "rasrap", seed, prec="fp64")
+        o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+        ms = _time_plan(lambda: p.execute(o), 2, flush)
+        th = o.cpu().numpy().reshape(M_REPL, -1)
+        p.close()
+        mr = 4
+        th_o, t_o = _timed_oracle(lambda: O.lmm_caplets(O.Sequence(O.RASRAP, N_FWD, M_REPL, seed), lm, K, N_PATHS,
+                                                        m_range=(0, mr), threads=T))
+        rel = float(np.max(np.abs(th[:mr] - th_o) / np.abs(th_o)))
+        pairs = lmm_fp64_pairs(N_FWD, N_PATHS * M_REPL)
+        out["lmm_caplets_40_N65536_M64_fp64_rasrap"] = {
+            "ms": ms, "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3),
+            "parity": {"ok": rel <= 1e-11, "tol": 1e-11, "max_rel_err": rel, "checked": f"replications 0..{mr - 1}, full N"},
+            "cpu_baseline": {"value": mr * N_PATHS * N_FWD / t_o, "unit": "path-steps/s", "cores": min(T, mr),
+                             "kind": "oracle", "sample": f"{mr} replications x N={N_PATHS}"},
+            "roofline": {"bound": "fp64", "pipe": "fp64 update pair (exp + reciprocal)",
+                         "achieved": round(pairs / (ms / 1e3) / 1e9, 3), "peak": round(pk.fp64_pair / 1e9, 3),
+                         "unit": "G FP64 update pairs/s", "frac": round(pairs / (ms / 1e3) / pk.fp64_pair, 4),
+                         "peak_source": f"probed: {pk.probe['fp64_pair']:.3f} pairs per SM per clock x {pk.sms} SMs x "
+                                        f"{pk.mhz:.0f} MHz"}}
+
+    # ---- MBS, 360 months, N = 65536, M = 64, FP32 + Kahan
+    if want("mbs"):
+        mb = inputs.mbs_paper(360)
+        res = {}
+        for s_ in SEQS:
+            p = rqmc.Plan.mbs(mb, N_PATHS, M_REPL, s_, seed, prec="fp32")
+            o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+            ms = _time_plan(lambda: p.execute(o), 3, flush)
+            th = o.cpu().numpy()
+            p.close()
+            q = O.Sequence(ids[s_], 360, M_REPL, seed, joe_kuo=jk)
+            th_o, t_o = _timed_oracle(lambda: _oracle_points(
+                lambda off, n: O.mbs_theta(q, mb, n, offset=off, m_range=(0, 1), threads=1), N_PATHS, T))
+            rel = float(abs(th[0] - th_o[0]) / abs(th_o[0]))
+            slots, fma = mbs_algorithmic_ops(360, N_PATHS * M_REPL)
+            res[s_] = {"ms": ms, "path_steps_per_s": N_PATHS * M_REPL * 360 / (ms / 1e3), "rq": float(th.mean()),
+                       "parity": {"ok": rel <= 1e-4, "tol": 1e-4, "max_rel_err": rel,
+                                  "checked": "replication 0 at full N"},
+                       "cpu_baseline": {"value": N_PATHS * 360 / t_o, "unit": "path-steps/s", "cores": T,
+                                        "kind": "oracle", "sample": f"replication 0 x N={N_PATHS} (point ranges)"},
+                       "roofline": pk.alu(slots, fma, ms / 1e3, f"mbs_kernel<float,{s_}>")}
+        out["mbs_360_N65536_M64_fp32"] = res
 
     # ---- adjoint Greeks: two-factor 80-forward strip, N = 2^18, M = 32, FP32 paths
-    cfg = inputs.CONFIGS["adjoint_2f_80"]
-    l2 = inputs.lmm_two_factor(cfg["n_fwd"], seed=cfg["seed"])
-    Na, Ma, nfa = cfg["N"], cfg["M"], cfg["n_fwd"]
-    w = np.ones(nfa)
-    p = rqmc.Plan.adjoint(l2, [0.05], w, Na, Ma, "sobol_ds", seed)
-    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
-    ms = _time_plan(lambda: p.execute(o), 2, flush)
-    ad = o.cpu().numpy().reshape(Ma, -1)
-    p.close()
-    q = O.Sequence(O.SOBOL_DS, 2 * nfa, Ma, seed, joe_kuo=jk)
-    (v_o, d_o, g_o), t_o = _timed_oracle(lambda: _oracle_points(
-        lambda off, n: O.lmm_adjoint(q, l2, [0.05], w, n, offset=off, m_range=(0, 1), threads=1), Na, T))
-    e_v = float(abs(ad[0, 0] - v_o[0]) / abs(v_o[0]))
-    e_d = float(np.max(np.abs(ad[0, 1:1 + nfa] - d_o[0]) / np.abs(d_o[0])))
-    e_g = float(np.max(np.abs(ad[0, 1 + nfa:1 + 2 * nfa] - g_o[0]) / np.abs(g_o[0])))
-    slots, fma = adjoint_algorithmic_ops(nfa, 2, Na * Ma)
-    out["adjoint_2f_80_N262144_M32_fp32_sobol"] = {
-        "ms": ms, "path_steps_per_s": Na * Ma * 2 * nfa / (ms / 1e3),
-        "parity": {"ok": max(e_v, e_d, e_g) <= 1e-4, "tol": 1e-4, "value_rel_err": e_v, "max_delta_rel_err": e_d,
-                   "max_vega_rel_err": e_g, "checked": "replication 0 at full N: value, 80 deltas, 80 vegas"},
-        "cpu_baseline": {"value": Na * 2 * nfa / t_o, "unit": "path-steps/s", "cores": T, "kind": "oracle",
-                         "sample": f"replication 0 x N={Na} (point ranges)"},
-        "roofline": pk.alu(slots, fma, ms / 1e3, "lmm_adjoint_kernel<80,2,sobol>")}
+    if want("adjoint"):
+        cfg = inputs.CONFIGS["adjoint_2f_80"]
+        l2 = inputs.lmm_two_factor(cfg["n_fwd"], seed=cfg["seed"])
+        Na, Ma, nfa = cfg["N"], cfg["M"], cfg["n_fwd"]
+        w = np.ones(nfa)
+        p = rqmc.Plan.adjoint(l2, [0.05], w, Na, Ma, "sobol_ds", seed)
+        o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+        ms = _time_plan(lambda: p.execute(o), 2, flush)
+        ad = o.cpu().numpy().reshape(Ma, -1)
+        p.close()
+        q = O.Sequence(O.SOBOL_DS, 2 * nfa, Ma, seed, joe_kuo=jk)
+        (v_o, d_o, g_o), t_o = _timed_oracle(lambda: _oracle_points(
+            lambda off, n: O.lmm_adjoint(q, l2, [0.05], w, n, offset=off, m_range=(0, 1), threads=1), Na, T))
+        e_v = float(abs(ad[0, 0] - v_o[0]) / abs(v_o[0]))
+        e_d = float(np.max(np.abs(ad[0, 1:1 + nfa] - d_o[0]) / np.abs(d_o[0])))
+        e_g = float(np.max(np.abs(ad[0, 1 + nfa:1 + 2 * nfa] - g_o[0]) / np.abs(g_o[0])))
+        slots, fma = adjoint_algorithmic_ops(nfa, 2, Na * Ma)
+        out["adjoint_2f_80_N262144_M32_fp32_sobol"] = {
+            "ms": ms, "path_steps_per_s": Na * Ma * 2 * nfa / (ms / 1e3),
+            "parity": {"ok": max(e_v, e_d, e_g) <= 1e-4, "tol": 1e-4, "value_rel_err": e_v, "max_delta_rel_err": e_d,
+                       "max_vega_rel_err": e_g, "checked": "replication 0 at full N: value, 80 deltas, 80 vegas"},
+            "cpu_baseline": {"value": Na * 2 * nfa / t_o, "unit": "path-steps/s", "cores": T, "kind": "oracle",
+                             "sample": f"replication 0 x N={Na} (point ranges)"},
+            "roofline": pk.alu(slots, fma, ms / 1e3, "lmm_adjoint_kernel<80,2,sobol>")}
 
     # ---- 512-instrument batch, one graph launch
-    desc = inputs.batch_instruments(seed)
-    insts = [dict(d, rate=0.05, vol=0.15, strike=0.05) if d["kind"] == "lmm" else d for d in desc]
-    Mb = 32
-    p = rqmc.Plan.batch(insts, Mb, "sobol_ds", seed)
-    o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
-    ms = _time_plan(lambda: p.execute(o), 1, flush)
-    parts = p.split_batch(o.cpu().numpy())
-    imb = p.batch_imbalance() if hasattr(p, "batch_imbalance") else None
-    p.close()
-    steps = sum(d["N"] * Mb * (d["n_fwd"] if d["kind"] == "lmm" else d["months"]) for d in desc)
-    slots = fma = 0.0
-    for d in desc:
-        if d["kind"] == "lmm":
-            s_, f_ = lmm_algorithmic_ops(d["n_fwd"], 1, d["N"] * Mb)
-        else:
-            s_, f_ = mbs_algorithmic_ops(d["months"], d["N"] * Mb)
-        slots, fma = slots + s_, fma + f_
-    sample = list(range(0, len(desc), 32))   # every 32nd instrument, replication 0, full N
+    if want("batch"):
+        desc = inputs.batch_instruments(seed)
+        insts = [dict(d, rate=0.05, vol=0.15, strike=0.05) if d["kind"] == "lmm" else d for d in desc]
+        Mb = 32
+        p = rqmc.Plan.batch(insts, Mb, "sobol_ds", seed)
+        o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
+        ms = _time_plan(lambda: p.execute(o), 1, flush)
+        parts = p.split_batch(o.cpu().numpy())
+        imb = p.batch_imbalance() if hasattr(p, "batch_imbalance") else None
+        p.close()
+        steps = sum(d["N"] * Mb * (d["n_fwd"] if d["kind"] == "lmm" else d["months"]) for d in desc)
+        slots = fma = 0.0
+        for d in desc:
+            if d["kind"] == "lmm":
+                s_, f_ = lmm_algorithmic_ops(d["n_fwd"], 1, d["N"] * Mb)
+            else:
+                s_, f_ = mbs_algorithmic_ops(d["months"], d["N"] * Mb)
+            slots, fma = slots + s_, fma + f_
+        sample = list(range(0, len(desc), 32))   # every 32nd instrument, replication 0, full N
 
-    def one(i):
-        d = insts[i]
-        if d["kind"] == "lmm":
-            lmi = inputs.lmm_flat(d["n_fwd"], delta=0.25, rate=d["rate"], vol=d["vol"])
-            return O.lmm_caplets(O.Sequence(O.SOBOL_DS, d["n_fwd"], Mb, seed, inst=i, joe_kuo=jk), lmi, [d["strike"]],
-                                 d["N"], m_range=(0, 1), threads=1)[0]
-        return O.mbs_theta(O.Sequence(O.SOBOL_DS, d["months"], Mb, seed, inst=i, joe_kuo=jk),
-                           inputs.mbs_paper(d["months"]), d["N"], m_range=(0, 1), threads=1)
+        def one(i):
+            d = insts[i]
+            if d["kind"] == "lmm":
+                lmi = inputs.lmm_flat(d["n_fwd"], delta=0.25, rate=d["rate"], vol=d["vol"])
+                return O.lmm_caplets(O.Sequence(O.SOBOL_DS, d["n_fwd"], Mb, seed, inst=i, joe_kuo=jk), lmi, [d["strike"]],
+                                     d["N"], m_range=(0, 1), threads=1)[0]
+            return O.mbs_theta(O.Sequence(O.SOBOL_DS, d["months"], Mb, seed, inst=i, joe_kuo=jk),
+                               inputs.mbs_paper(d["months"]), d["N"], m_range=(0, 1), threads=1)
 
-    def run_sample():
-        with ThreadPoolExecutor(T) as ex:
-            return list(ex.map(one, sample))
-    ref, t_o = _timed_oracle(run_sample)
-    rel = max(float(np.max(np.abs(parts[i][0] - r) / np.abs(r))) for i, r in zip(sample, ref))
-    o_steps = sum(desc[i]["N"] * (desc[i]["n_fwd"] if desc[i]["kind"] == "lmm" else desc[i]["months"]) for i in sample)
-    out["batch_512_M32_fp32_sobol"] = {
-        "ms": ms, "path_steps_per_s": steps / (ms / 1e3), "path_steps": steps,
-        "imbalance_max_sm_busy_over_mean": imb,
-        "parity": {"ok": rel <= 1e-4, "tol": 1e-4, "max_rel_err": rel,
-                   "checked": f"{len(sample)} instruments (every 32nd), replication 0, full N"},
-        "cpu_baseline": {"value": o_steps / t_o, "unit": "path-steps/s", "cores": T, "kind": "oracle",
-                         "sample": f"{len(sample)} instruments x replication 0"},
-        "roofline": pk.alu(slots, fma, ms / 1e3, "batch_kernel<sobol, 3 work classes>")}
+        def run_sample():
+            with ThreadPoolExecutor(T) as ex:
+                return list(ex.map(one, sample))
+        ref, t_o = _timed_oracle(run_sample)
+        rel = max(float(np.max(np.abs(parts[i][0] - r) / np.abs(r))) for i, r in zip(sample, ref))
+        o_steps = sum(desc[i]["N"] * (desc[i]["n_fwd"] if desc[i]["kind"] == "lmm" else desc[i]["months"]) for i in sample)
+        out["batch_512_M32_fp32_sobol"] = {
+            "ms": ms, "path_steps_per_s": steps / (ms / 1e3), "path_steps": steps,
+            "imbalance_max_sm_busy_over_mean": imb,
+            "parity": {"ok": rel <= 1e-4, "tol": 1e-4, "max_rel_err": rel,
+                       "checked": f"{len(sample)} instruments (every 32nd), replication 0, full N"},
+            "cpu_baseline": {"value": o_steps / t_o, "unit": "path-steps/s", "cores": T, "kind": "oracle",
+                             "sample": f"{len(sample)} instruments x replication 0"},
+            "roofline": pk.alu(slots, fma, ms / 1e3, "batch_kernel<sobol, 3 work classes>")}
 
     # ---- Sec. 5's Treasury-curve study: caplet on L_10 (T = 5, delta = 0.5, K = 1 %, sigma = 4 %)
-    # from the 24 Feb 2012 curve; std of M = 100 independent estimates, time and efficiency
-    # (std x time) against N, and the fitted convergence rate of the std
-    st = inputs.TREASURY_STUDY
-    lmt = inputs.lmm_treasury(st["T"], st["delta"], st["vol"])
-    study = {}
-    for s_ in SEQS + ("sobol_lms",):
-        rows = []
-        for e in range(10, 21, 2):
-            pt = rqmc.Plan.caplets(lmt, [st["K"]], 1 << e, st["M"], s_, seed, prec="fp32")
-            ot = torch.empty(pt.output_size(), dtype=torch.float64, device=dev)
-            ms = _time_plan(lambda: pt.execute(ot), 3, flush)
-            th_all = ot.cpu().numpy().reshape(st["M"], -1)
-            th = th_all[:, lmt["n_fwd"] - 1]
-            pt.close()
-            rows.append({"N": 1 << e, "rq": float(th.mean()), "std": float(th.std(ddof=1)), "ms": ms,
-                         "efficiency": float(th.std(ddof=1)) * ms})
-            if e == 14:   # parity at N = 2^14: every replication, the study's caplet and the whole strip
-                sid = {"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX, "sobol_lms": O.SOBOL_LMS}[s_]
-                th_o = O.lmm_caplets(O.Sequence(sid, lmt["n_fwd"], st["M"], seed, joe_kuo=jk), lmt, [st["K"]],
-                                     1 << e, threads=T)
-                c = lmt["n_fwd"] - 1
-                rel14 = float(np.max(np.abs(th_all[:, c] - th_o[:, c]) / np.abs(th_o[:, c])))
-                abs14 = float(np.max(np.abs(th_all - th_o)))
-                ok14 = rel14 <= 1e-4 and bool(np.all(np.abs(th_all - th_o) <= 1e-4 * np.abs(th_o) + 1e-9))
-        lx = np.log([r["N"] for r in rows])
-        ly = np.log([r["std"] for r in rows])
-        study[s_] = {"rate": float(np.polyfit(lx, ly, 1)[0]), "by_N": rows,
-                     "parity": {"ok": ok14, "tol": "1e-4 relative on the study's caplet (L_10); 1e-4 |theta| + 1e-9 "
-                                "on every caplet of the strip (the early ones are worth 0 at K = 1 %)",
-                                "study_caplet_max_rel_err": rel14, "strip_max_abs_err": abs14,
-                                "checked": "N = 2^14, all 100 replications, all 10 caplets"}}
-    out["lmm_treasury_study_T5_M100_fp32"] = study
+    if want("treasury"):
+        # from the 24 Feb 2012 curve; std of M = 100 independent estimates, time and efficiency
+        # (std x time) against N, and the fitted convergence rate of the std
+        st = inputs.TREASURY_STUDY
+        lmt = inputs.lmm_treasury(st["T"], st["delta"], st["vol"])
+        study = {}
+        for s_ in SEQS + ("sobol_lms",):
+            rows = []
+            for e in range(10, 21, 2):
+                pt = rqmc.Plan.caplets(lmt, [st["K"]], 1 << e, st["M"], s_, seed, prec="fp32")
+                ot = torch.empty(pt.output_size(), dtype=torch.float64, device=dev)
+                ms = _time_plan(lambda: pt.execute(ot), 3, flush)
+                th_all = ot.cpu().numpy().reshape(st["M"], -1)
+                th = th_all[:, lmt["n_fwd"] - 1]
+                pt.close()
+                rows.append({"N": 1 << e, "rq": float(th.mean()), "std": float(th.std(ddof=1)), "ms": ms,
+                             "efficiency": float(th.std(ddof=1)) * ms})
+                if e == 14:   # parity at N = 2^14: every replication, the study's caplet and the whole strip
+                    sid = {"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX, "sobol_lms": O.SOBOL_LMS}[s_]
+                    th_o = O.lmm_caplets(O.Sequence(sid, lmt["n_fwd"], st["M"], seed, joe_kuo=jk), lmt, [st["K"]],
+                                         1 << e, threads=T)
+                    c = lmt["n_fwd"] - 1
+                    rel14 = float(np.max(np.abs(th_all[:, c] - th_o[:, c]) / np.abs(th_o[:, c])))
+                    abs14 = float(np.max(np.abs(th_all - th_o)))
+                    ok14 = rel14 <= 1e-4 and bool(np.all(np.abs(th_all - th_o) <= 1e-4 * np.abs(th_o) + 1e-9))
+            lx = np.log([r["N"] for r in rows])
+            ly = np.log([r["std"] for r in rows])
+            study[s_] = {"rate": float(np.polyfit(lx, ly, 1)[0]), "by_N": rows,
+                         "parity": {"ok": ok14, "tol": "1e-4 relative on the study's caplet (L_10); 1e-4 |theta| + 1e-9 "
+                                    "on every caplet of the strip (the early ones are worth 0 at K = 1 %)",
+                                    "study_caplet_max_rel_err": rel14, "strip_max_abs_err": abs14,
+                                    "checked": "N = 2^14, all 100 replications, all 10 caplets"}}
+        out["lmm_treasury_study_T5_M100_fp32"] = study
 
     # ---- Matousek-scrambled Sobol' on the headline caplet workload (same kernel, scrambled tables)
-    pl_ = rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, "sobol_lms", seed, prec="fp32")
-    o_ = torch.empty(pl_.output_size(), dtype=torch.float64, device=dev)
-    ms = _time_plan(lambda: pl_.execute(o_), 3, flush)
-    th = o_.cpu().numpy().reshape(M_REPL, -1)
-    pl_.close()
-    th_o, t_o = _timed_oracle(lambda: O.lmm_caplets(O.Sequence(O.SOBOL_LMS, N_FWD, M_REPL, seed, joe_kuo=jk), lm, K,
-                                                    N_PATHS, m_range=(0, 4), threads=T))
-    e = float(caplet_scaled_err(th[:4], th_o, len(K)).max())
-    mufu, fma = lmm_algorithmic_ops(N_FWD, len(K), N_PATHS * M_REPL)
-    out["lmm_caplets_40_N65536_M64_fp32_sobol_lms"] = {
-        "ms": ms, "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3),
-        "parity": {"ok": e <= 1e-4, "tol": 1e-4, "max_scaled_err": e, "checked": "replications 0..3, full N"},
-        "cpu_baseline": {"value": 4 * N_PATHS * N_FWD / t_o, "unit": "path-steps/s", "cores": min(T, 4),
-                         "kind": "oracle", "sample": f"4 replications x N={N_PATHS}"},
-        "roofline": pk.alu(mufu, fma, ms / 1e3, "lmm_caplet_kernel<40,sobol,float>")}
+    if want("lms"):
+        pl_ = rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, "sobol_lms", seed, prec="fp32")
+        o_ = torch.empty(pl_.output_size(), dtype=torch.float64, device=dev)
+        ms = _time_plan(lambda: pl_.execute(o_), 3, flush)
+        th = o_.cpu().numpy().reshape(M_REPL, -1)
+        pl_.close()
+        th_o, t_o = _timed_oracle(lambda: O.lmm_caplets(O.Sequence(O.SOBOL_LMS, N_FWD, M_REPL, seed, joe_kuo=jk), lm, K,
+                                                        N_PATHS, m_range=(0, 4), threads=T))
+        e = float(caplet_scaled_err(th[:4], th_o, len(K)).max())
+        mufu, fma = lmm_algorithmic_ops(N_FWD, len(K), N_PATHS * M_REPL)
+        out["lmm_caplets_40_N65536_M64_fp32_sobol_lms"] = {
+            "ms": ms, "path_steps_per_s": N_PATHS * M_REPL * N_FWD / (ms / 1e3),
+            "parity": {"ok": e <= 1e-4, "tol": 1e-4, "max_scaled_err": e, "checked": "replications 0..3, full N"},
+            "cpu_baseline": {"value": 4 * N_PATHS * N_FWD / t_o, "unit": "path-steps/s", "cores": min(T, 4),
+                             "kind": "oracle", "sample": f"4 replications x N={N_PATHS}"},
+            "roofline": pk.alu(mufu, fma, ms / 1e3, "lmm_caplet_kernel<40,sobol,float>")}
 
     # ---- point stream: s = 360, N = 65536, M = 64 FP32 normals and uniforms, written to HBM
-    buf = torch.empty((M_REPL, 360, N_PATHS), dtype=torch.float32, device=dev)
-    res = {}
-    for s_ in SEQS:
-        row = {}
-        for tr in ("normal", "uniform"):
-            pp = rqmc.Plan.points(360, N_PATHS, M_REPL, s_, seed, prec="fp32", transform=tr)
-            ms = _time_plan(lambda: pp.execute(buf), 3, flush)   # kernel only: tables built once
-            pp.close()
-            gbs = buf.numel() * 4 / (ms / 1e3) / 1e9
-            q = O.Sequence(ids[s_], 360, 1, seed, joe_kuo=jk)
-            ref = q.points(4096, transform=O.NORMAL if tr == "normal" else O.UNIFORM, threads=T)[0, :, :]
-            got = buf[0, :, :4096].cpu().numpy().astype(np.float64)
-            err = float(np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref)))) if tr == "normal" else \
-                float(np.max(np.abs(got - ref) / ref))
-            tol = 1e-6 if tr == "normal" else 4e-7
-            row[tr] = {"ms": ms, "GB_per_s": gbs, "gnumbers_per_s": buf.numel() / (ms / 1e3) / 1e9,
-                       "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk.hbm_gbs, "unit": "GB/s",
-                                    "frac": round(gbs / pk.hbm_gbs, 4), "peak_source": pk.hbm_src},
-                       "parity": {"ok": err <= tol, "tol": tol, "max_err": err,
-                                  "checked": "replication 0, all 360 dimensions, points 0..4095"}}
-        ms1 = _time_plan(lambda: rqmc.rqmc_points(360, N_PATHS, M_REPL, s_, seed, transform="normal", out=buf), 2,
-                         flush)   # one-shot call: tables + kernel
-        row["one_shot_normal_ms"] = ms1
-        res[s_] = row
-    out["points_s360_N65536_M64_fp32"] = res
-    del buf
+    if want("points"):
+        Mp = args.points_m
+        buf = torch.empty((Mp, 360, N_PATHS), dtype=torch.float32, device=dev)
+        res = {}
+        for s_ in SEQS:
+            row = {}
+            for tr in ("normal", "uniform"):
+                pp = rqmc.Plan.points(360, N_PATHS, Mp, s_, seed, prec="fp32", transform=tr)
+                ms = _time_plan(lambda: pp.execute(buf), 3, flush)   # kernel only: tables built once
+                pp.close()
+                gbs = buf.numel() * 4 / (ms / 1e3) / 1e9
+                q = O.Sequence(ids[s_], 360, 1, seed, joe_kuo=jk)
+                ref = q.points(4096, transform=O.NORMAL if tr == "normal" else O.UNIFORM, threads=T)[0, :, :]
+                got = buf[0, :, :4096].cpu().numpy().astype(np.float64)
+                err = float(np.max(np.abs(got - ref) / np.maximum(1.0, np.abs(ref)))) if tr == "normal" else \
+                    float(np.max(np.abs(got - ref) / ref))
+                tol = 1e-6 if tr == "normal" else 4e-7
+                row[tr] = {"ms": ms, "GB_per_s": gbs, "gnumbers_per_s": buf.numel() / (ms / 1e3) / 1e9,
+                           "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk.hbm_gbs, "unit": "GB/s",
+                                        "frac": round(gbs / pk.hbm_gbs, 4), "peak_source": pk.hbm_src},
+                           "parity": {"ok": err <= tol, "tol": tol, "max_err": err,
+                                      "checked": "replication 0, all 360 dimensions, points 0..4095"}}
+            ms1 = _time_plan(lambda: rqmc.rqmc_points(360, N_PATHS, Mp, s_, seed, transform="normal", out=buf), 2,
+                             flush)   # one-shot call: tables + kernel
+            row["one_shot_normal_ms"] = ms1
+            res[s_] = row
+        out[f"points_s360_N65536_M{Mp}_fp32"] = res
+        del buf
     return out
 
 
@@ -679,6 +693,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle legs (cpu_baseline and parity)")
     ap.add_argument("--no-extra", action="store_true", help="skip the other-configuration figures")
+    ap.add_argument("--extra", default="all",
+                    help="comma-separated subset of the other configurations: product, fp64, mbs, adjoint, batch, "
+                         "treasury, lms, points (default all)")
+    ap.add_argument("--points-m", type=int, default=M_REPL,
+                    help="replications of the point-stream figure (default 64; smaller for profiler captures)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

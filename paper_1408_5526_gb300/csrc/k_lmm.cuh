@@ -17,7 +17,8 @@
 // per step t and forward n, the constant g = 2^(-t cc_n) from a table, so that 1 + 2^-X =
 // 1 + g 2^-X~ is one FMA.  Two lockstep paths share one reciprocal, 1/d0 = d1 / (d0 d1) and
 // 1/d1 = d0 / (d0 d1), multiplied once by h sigma_n: per forward and pair of paths two ex2,
-// one rcp and eight FP32 operations.  Forward n sits in slot n-1 of an
+// one rcp and eight FP32 operations.  Single-path strips (80 and 160 forwards) pair adjacent
+// forwards the same way outside the first group of a block.  Forward n sits in slot n-1 of an
 // NF-slot array (NF = 16/40/80/160).  Steps run in blocks of 8; after each block the
 // array shifts down by 8 slots, so at step tp of a block the alive slots are tp..7 of
 // group 0 (entered through an 8-way fall-through switch) plus whole groups of 8 that a
@@ -246,10 +247,28 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
 #pragma unroll
             for (int gi = 1; gi < NF / 8; ++gi) {
                 if (gi < ngrp) {
+                    if constexpr (P == 1 && sizeof(T) == 4 && SEQ != kPhilox) {
+                        // one path: adjacent forwards share a reciprocal, 1/d_k = d_(k+1) r and
+                        // 1/d_(k+1) = d_k r with r = 1/(d_k d_(k+1)).  (Not for Philox: its cached
+                        // counter words already press these strips' registers.)
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const CC c = M::lds(cb + 8 * gi + k);
-                        update_slot(8 * gi + k, c);
+                        for (int k = 0; k < 8; k += 2) {
+                            const CC c0 = M::lds(cb + 8 * gi + k), c1 = M::lds(cb + 8 * gi + k + 1);
+                            T &x0 = X[0][8 * gi + k], &x1 = X[0][8 * gi + k + 1];
+                            const T e0 = M::expb(-x0), e1 = M::expb(-x1);
+                            const T d0 = GT ? fmaT(e0, c0.z, T(1)) : T(1) + e0, d1 = GT ? fmaT(e1, c1.z, T(1)) : T(1) + e1;
+                            const T r = M::rcp(d0 * d1);
+                            W[0] = fmaT(c0.y * r, d1, W[0]);
+                            x0 = GT ? fmaT(c0.x, W[0], x0) : fmaT(c0.x, W[0], x0) + c0.z;
+                            W[0] = fmaT(c1.y * r, d0, W[0]);
+                            x1 = GT ? fmaT(c1.x, W[0], x1) : fmaT(c1.x, W[0], x1) + c1.z;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const CC c = M::lds(cb + 8 * gi + k);
+                            update_slot(8 * gi + k, c);
+                        }
                     }
                 }
             }
