@@ -77,16 +77,20 @@ typedef enum {
 } rqmc_sequence;
 typedef enum { RQMC_FP64 = 0, RQMC_FP32 = 1 } rqmc_precision;
 typedef enum { RQMC_UNIFORM = 0, RQMC_NORMAL = 1, RQMC_RAW = 2 } rqmc_transform;
-typedef enum { RQMC_LOG_EULER = 0 } rqmc_lmm_scheme;
+typedef enum { RQMC_LOG_EULER = 0, RQMC_EULER = 1 } rqmc_lmm_scheme;
 
 /* LIBOR market model (Sec. 5): forwards L_1..L_nf over [T_n, T_{n+1}], T_n = n*delta,
- * simulated on the grid t_i = T_i under the spot measure with log-Euler steps of
- * eq. (L_n_discrete); L_0 is fixed at t = 0.  sigma_n = vol[n-1] * b_n with unit
- * loading rows b_n (d = n_factors).  All arrays are host memory, read during the call. */
+ * simulated on the grid t_i = T_i under the spot measure; L_0 is fixed at t = 0.
+ * sigma_n = vol[n-1] * b_n with unit loading rows b_n (d = n_factors).  Schemes:
+ * RQMC_EULER is eq. (L_n_discrete) as printed, L_n += mu_n L_n h + L_n sqrt(h) sigma_n.Z;
+ * RQMC_LOG_EULER applies the same drift and noise to log L_n with the Ito correction,
+ * log L_n += (mu_n - |sigma_n|^2 / 2) h + sqrt(h) sigma_n.Z.  price_caplets and the caplet
+ * plans run both; the adjoint and the batch run log-Euler.  All arrays are host memory,
+ * read during the call. */
 typedef struct {
     int n_fwd;               /* nf >= 1 */
     int n_factors;           /* d in {1, 2} */
-    int scheme;              /* RQMC_LOG_EULER */
+    int scheme;              /* rqmc_lmm_scheme */
     int reserved;
     double delta;            /* accrual period = time step, > 0 */
     const double *L0;        /* [nf+1]: L_0(0), L_1(0), ..., L_nf(0) (eq. BL from bond prices) */

@@ -136,8 +136,10 @@ int lmm_bucket(int nf) {
 
 template <typename T>
 void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK, int bucket) {
+    const bool euler = p->scheme == RQMC_EULER;
     const double h = p->delta, sh = std::sqrt(p->delta);
-    const double sc = sizeof(T) == 4 ? 1.4426950408889634 : 1.0;   // FP32 works in base 2
+    // FP32 log-Euler works in base 2; Euler carries delta L itself, in natural units
+    const double sc = (sizeof(T) == 4 && !euler) ? 1.4426950408889634 : 1.0;
     md = LmmModel<T>{};
     md.nf = p->n_fwd;
     md.nK = nK;
@@ -153,8 +155,8 @@ void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK
         const double L0 = real ? p->L0[n] : p->L0[p->n_fwd];
         const double sg = real ? p->vol[n - 1] : 0.0;
         md.sig[slot] = (T)sg;
-        md.cc[slot] = (T)(-0.5 * sg * sg * h * sc);
-        md.X0[slot] = (T)(std::log(p->delta * L0) * sc);
+        md.cc[slot] = euler ? T(0) : (T)(-0.5 * sg * sg * h * sc);
+        md.X0[slot] = euler ? (T)(p->delta * L0) : (T)(std::log(p->delta * L0) * sc);
     }
 }
 
@@ -169,7 +171,8 @@ rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool ad
         return adjoint ? RQMC_EINVAL : RQMC_EUNSUPPORTED;
     }
     if (p->n_factors > 1 && !p->loadings) { set_error("loadings required for n_factors > 1"); return RQMC_EINVAL; }
-    if (p->scheme != RQMC_LOG_EULER) { set_error("only the log-Euler scheme is built"); return RQMC_EUNSUPPORTED; }
+    if (p->scheme != RQMC_LOG_EULER && p->scheme != RQMC_EULER) { set_error("unknown scheme"); return RQMC_EINVAL; }
+    if (adjoint && p->scheme != RQMC_LOG_EULER) { set_error("the adjoint runs the log-Euler scheme"); return RQMC_EUNSUPPORTED; }
     if (!(p->delta > 0.0) || !std::isfinite(p->delta)) { set_error("delta must be > 0"); return RQMC_EINVAL; }
     if (!finite_all(p->L0, p->n_fwd + 1) || !finite_all(p->vol, p->n_fwd)) {
         set_error("L0/vol must be finite");
@@ -177,7 +180,7 @@ rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool ad
     }
     if (!(p->L0[0] > -1.0 / p->delta)) { set_error("1 + delta L_0(0) must be positive"); return RQMC_EINVAL; }
     for (int n = 1; n <= p->n_fwd; ++n)
-        if (!(p->L0[n] > 0.0)) { set_error("log-Euler needs positive initial forwards L_n(0), n >= 1"); return RQMC_EINVAL; }
+        if (!(p->L0[n] > 0.0)) { set_error("initial forwards L_n(0), n >= 1, must be positive"); return RQMC_EINVAL; }
     if (!K || nK < 1 || nK > kMaxStrikes || !finite_all(K, nK)) {
         set_error("strikes: 1..8 finite values");
         return RQMC_EINVAL;
@@ -280,6 +283,7 @@ extern "C" rqmc_status rqmc_plan_caplets(const rqmc_lmm_params *p, const double 
     if (rs != RQMC_OK) return rs;
     const int nout = p->n_fwd * n_strikes;
     pl->nf_bucket = lmm_bucket(p->n_fwd);
+    pl->scheme = p->scheme;
     set_reduction(*pl, nout, 256, prec == RQMC_FP32 ? 2 : 1);
     if (prec == RQMC_FP32) fill_lmm(pl->lmm32, p, strikes_host, n_strikes, pl->nf_bucket);
     else fill_lmm(pl->lmm64, p, strikes_host, n_strikes, pl->nf_bucket);

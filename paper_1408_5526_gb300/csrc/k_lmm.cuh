@@ -85,6 +85,15 @@ __device__ __forceinline__ void lmm_update(T &X, const typename LmmMath<T>::C c,
     X = GT ? fmaT(c.x, W, X) : fmaT(c.x, W, X) + c.z;
 }
 
+// One forward of one path under the Euler scheme (eq. L_n_discrete), X = delta L:
+// a = X / (1 + X), W += h sigma a, X *= 1 + sigma W.
+template <typename T>
+__device__ __forceinline__ void lmm_update_euler(T &X, const typename LmmMath<T>::C c, T &W) {
+    const T a = X * LmmMath<T>::rcp(T(1) + X);
+    W = fmaT(c.y, a, W);
+    X = fmaT(X * c.x, W, X);
+}
+
 // The same forward for two lockstep paths with one reciprocal: t = h sigma / (d0 d1), so
 // h sigma a_0 = t d1 and h sigma a_1 = t d0.
 template <bool GT, typename T>
@@ -122,14 +131,14 @@ struct LmmScal {
 // (sigma_n, h sigma_n, 2^(-t cc_n), 2^(t cc_n)); otherwise [NF] of (sigma_n, h sigma_n, cc_n, 0).
 template <int NF, typename T>
 __host__ __device__ constexpr size_t lmm_cst_count() {
-    return lmm_gtab<NF, T>() ? (size_t)NF * (NF + 1) : (size_t)NF;
+    return lmm_gtab<NF, T>() ? (size_t)NF * (NF + 1) : (size_t)NF;   // the Euler scheme uses the first NF
 }
 
 // Fill the constants and the initial state X0 (all threads of the CTA; the caller synchronises).
-template <int NF, typename T>
+template <int NF, typename T, bool EU = false>
 __device__ __forceinline__ void lmm_fill_constants(const LmmModel<T> &md, typename LmmMath<T>::C *cst, T *X0) {
     using CC = typename LmmMath<T>::C;
-    if constexpr (lmm_gtab<NF, T>()) {
+    if constexpr (lmm_gtab<NF, T>() && !EU) {
         for (int k = threadIdx.x; k < NF * (NF + 1); k += blockDim.x) {
             const int t = k / NF, n = k % NF;
             const float x = (float)t * md.cc[n];   // t cc_n in log2 units
@@ -177,14 +186,14 @@ constexpr int lmm_min_blocks() {
 // the P paths) into the warp's transpose buffer, block sums into the warp's Kahan
 // accumulators (wacc/wcmp, indexed by output t nK + k).  The P paths share every constant
 // load and all control flow, and give each warp P independent dependency chains.
-template <int NF, int SEQ, typename T, int P>
+template <int NF, int SEQ, typename T, int P, bool EU = false>
 __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&active)[P], const LmmScal<T> &sc,
                                          const typename LmmMath<T>::C *cst, const T *X0, const T *Ks, T *zb,
                                          T *wbuf, T *wacc, T *wcmp, const int lane) {
     using M = LmmMath<T>;
     using CC = typename M::C;
     constexpr int PAD = M::PAD;
-    constexpr bool GT = lmm_gtab<NF, T>();
+    constexpr bool GT = lmm_gtab<NF, T>() && !EU;
     const int nf = sc.nf, nK = sc.nK;
     const T sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
     const int zs = P * blockDim.x;   // stride of one step in the normals buffer
@@ -223,7 +232,10 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
             const CC *cb = GT ? cb0 + (size_t)(8 * b + tp) * NF : cb0;   // this step's row
             // slot k of the P paths: FP32 pairs share a reciprocal, an odd path goes alone
             auto update_slot = [&](const int k, const CC c) {
-                if constexpr (sizeof(T) == 4) {
+                if constexpr (EU) {
+#pragma unroll
+                    for (int p = 0; p < P; ++p) lmm_update_euler<T>(X[p][k], c, W[p]);
+                } else if constexpr (sizeof(T) == 4) {
 #pragma unroll
                     for (int p = 0; p + 1 < P; p += 2) lmm_update2<GT, T>(X[p][k], X[p + 1][k], c, W[p], W[p + 1]);
                     if constexpr (P % 2 == 1) lmm_update<GT, T>(X[P - 1][k], c, W[P - 1]);
@@ -247,7 +259,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
 #pragma unroll
             for (int gi = 1; gi < NF / 8; ++gi) {
                 if (gi < ngrp) {
-                    if constexpr (P == 1 && sizeof(T) == 4 && SEQ != kPhilox) {
+                    if constexpr (P == 1 && sizeof(T) == 4 && SEQ != kPhilox && !EU) {
                         // one path: adjacent forwards share a reciprocal, 1/d_k = d_(k+1) r and
                         // 1/d_(k+1) = d_k r with r = 1/(d_k d_(k+1)).  (Not for Philox: its cached
                         // counter words already press these strips' registers.)
@@ -291,7 +303,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
             const T gfix = GT ? cst[(size_t)(8 * b + tp + 1) * NF + 8 * b + tp].w : T(1);
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const T e = GT ? M::expb(Xf[p]) * gfix : M::expb(Xf[p]);
+                const T e = EU ? Xf[p] : (GT ? M::expb(Xf[p]) * gfix : M::expb(Xf[p]));   // delta L
                 disc[p] *= M::rcp(T(1) + e);
                 Lf[p] = e * inv_dl;
                 dd[p] = active[p] ? dl * disc[p] : T(0);
@@ -338,7 +350,7 @@ constexpr int lmm_ilp() {
 #endif
 }
 
-template <int NF, int SEQ, typename T>
+template <int NF, int SEQ, typename T, bool EU>
 __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kernel(const GenParams g, const LmmModel<T> md, const RedParams r) {
     using M = LmmMath<T>;
     using CC = typename M::C;
@@ -357,7 +369,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     T *acc = reinterpret_cast<T *>(smem_raw + o_acc);
     T *cmp = acc + nw * nout;
     T *wacc = acc + warp * nout, *wcmp = cmp + warp * nout;
-    lmm_fill_constants<NF, T>(md, cst, X0);
+    lmm_fill_constants<NF, T, EU>(md, cst, X0);
     if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md.K[threadIdx.x];
     zero_acc(acc, cmp, nw * nout);
     const LmmScal<T> sc{md.nf, md.nK, md.dl, md.inv_dl, md.disc0, md.hc, md.sqhc};
@@ -386,7 +398,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
                 pg[p].init(gv, active[p] ? i : 0u);
             }
             if (!__any_sync(0xffffffffu, any)) break;
-            lmm_path<NF, SEQ, T, P>(pg, active, sc, cst, X0, Ks, zb, wbuf, wacc, wcmp, lane);
+            lmm_path<NF, SEQ, T, P, EU>(pg, active, sc, cst, X0, Ks, zb, wbuf, wacc, wcmp, lane);
         }
         flush_unit(r, u, acc, cmp);
     }
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
 
 template <int NF, int SEQ, typename T>
 static cudaError_t launch_lmm_t(const Plan &pl, const LmmModel<T> &md, cudaStream_t st) {
-    auto kern = lmm_caplet_kernel<NF, SEQ, T>;
+    auto kern = pl.scheme == RQMC_EULER ? lmm_caplet_kernel<NF, SEQ, T, true> : lmm_caplet_kernel<NF, SEQ, T, false>;
     const int threads = pl.threads;
     size_t a, b, c, d, e2;
     const size_t smem =

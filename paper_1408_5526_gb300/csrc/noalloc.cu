@@ -91,6 +91,7 @@ extern "C" rqmc_status rqmc_price_caplets_noalloc(const rqmc_lmm_params *p, cons
     pl.seed = seed;
     pl.inst = 0;
     pl.nf_bucket = lmm_bucket(p->n_fwd);
+    pl.scheme = p->scheme;
     const int nout = p->n_fwd * n_strikes;
     set_reduction(pl, nout, 256, prec == RQMC_FP32 ? 2 : 1);
     if (prec == RQMC_FP32) fill_lmm(pl.lmm32, p, strikes_host, n_strikes, pl.nf_bucket);

@@ -29,9 +29,11 @@ struct RedParams {
     uint32_t *status;        // device status word (0 = ok)
 };
 
-// One-factor LMM in log space: X_n = log(delta L_n) (FP32: log2), so that
-// delta L/(1 + delta L) = 1/(1 + b^-X) and one log-Euler step is
+// One-factor LMM.  Log-Euler: X_n = log(delta L_n) (FP32: log2), so that
+// delta L/(1 + delta L) = 1/(1 + b^-X) and one step is
 // X_n += sigma_n (h S_n + sqrt(h) Z) - sigma_n^2 h / 2 (times log2 e in FP32).
+// Euler: X_n = delta L_n itself and one step is X_n *= 1 + sigma_n (h S_n + sqrt(h) Z)
+// (hc = h, sqhc = sqrt(h), cc unused).
 template <typename T>
 struct LmmModel {
     int nf, nK;
@@ -144,6 +146,7 @@ struct Plan {
     RedParams red{};
     int threads = 256, ppt = 4, grid = 0;
     int nf_bucket = 0;
+    int scheme = RQMC_LOG_EULER;   // caplet plans: rqmc_lmm_scheme
     int transform = 0;       // point-stream plans: RQMC_UNIFORM / RQMC_NORMAL / RQMC_RAW
     int launches = 0;
     // device memory (one allocation)

@@ -170,6 +170,43 @@ def test_caplets_full_size_sampled(R, seq):
         assert np.all(np.abs(th32[m:m + 1] - th_o) <= _caplet_tol(th_o, len(K)))
 
 
+@pytest.mark.parametrize("seq,nf", [(O.RASRAP, 40), (O.SOBOL_DS, 40), (O.PHILOX, 40), (O.SOBOL_LMS, 16),
+                                    (O.SOBOL_DS, 80), (O.RASRAP, 160), (O.HALTON_RS, 7)])
+def test_caplets_euler_scheme(R, seq, nf):
+    """The Euler scheme of eq. (L_n_discrete) (delta L carried linearly, X *= 1 + sigma W)
+    against the oracle's Euler branch, FP64 and FP32, across the register buckets."""
+    lm = inputs.lmm_flat(nf, vol=0.2, scheme=1)
+    lm["L0"] = np.linspace(0.045, 0.055, nf + 1)
+    K = inputs.LMM_STRIKES
+    N, M = 2000, 2
+    th_o = O.lmm_caplets(O.Sequence(seq, nf, M, 6, joe_kuo=JK), lm, K, N)
+    th64, _, _ = R.price_caplets(lm, K, N, M, seq, 6, prec="fp64")
+    np.testing.assert_allclose(th64, th_o, rtol=1e-11, atol=1e-15)
+    th32, _, _ = R.price_caplets(lm, K, N, M, seq, 6, prec="fp32")
+    assert np.all(np.abs(th32 - th_o) <= _caplet_tol(th_o, len(K)))
+    # the log-Euler result differs: the scheme is really switched
+    le, _, _ = R.price_caplets(dict(lm, scheme=0), K, N, M, seq, 6, prec="fp64")
+    assert np.max(np.abs(le - th64)) > 1e-6 * np.abs(th64).max()
+
+
+def test_caplets_euler_zero_volatility_and_refusals(R):
+    # sigma = 0: the Euler step is the identity, the closed form of eq. BL
+    nf, dl = 12, 0.25
+    lm = inputs.lmm_flat(nf, vol=0.0, scheme=1)
+    lm["L0"] = np.linspace(0.03, 0.07, nf + 1)
+    K = inputs.LMM_STRIKES
+    th, _, _ = R.price_caplets(lm, K, 1000, 2, "sobol_ds", 1, prec="fp64")
+    B = np.concatenate([[1.0], np.cumprod(1.0 / (1.0 + dl * lm["L0"]))])
+    want = np.array([[dl * B[n + 1] * max(lm["L0"][n] - k, 0.0) for k in K] for n in range(1, nf + 1)]).reshape(-1)
+    np.testing.assert_allclose(th[0], want, rtol=1e-13, atol=1e-15)
+    with pytest.raises(R.RqmcError) as e:   # the adjoint runs log-Euler only
+        R.price_adjoint(inputs.lmm_flat(8, scheme=1), [0.05], np.ones(8), 64, 1, "philox", 1)
+    assert e.value.status == 5
+    with pytest.raises(R.RqmcError) as e:   # unknown scheme
+        R.price_caplets(inputs.lmm_flat(8, scheme=7), [0.05], 64, 1, "philox", 1)
+    assert e.value.status == 1
+
+
 # ------------------------------------------------------------------ MBS
 @pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS, O.SOBOL_LMS])
 def test_mbs_small(R, seq):

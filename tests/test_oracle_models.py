@@ -121,6 +121,50 @@ def test_lmm_first_two_caplets_match_quadrature():
         assert abs(rq[1] - cap2) <= 4 * sd[1] / 4 + 1e-9 * cap2, (rq[1], cap2, sd[1])
 
 
+def test_lmm_euler_first_two_caplets_match_quadrature():
+    """The Euler scheme of eq. (L_n_discrete), L_n <- L_n + mu_n L_n h + L_n sqrt(h) sigma_n Z with
+    mu_n = sum_{j<=n} delta L_j sigma_n sigma_j / (1 + delta L_j): the first two caplets of a
+    flat one-factor curve against quadrature of the same discrete model (one and two steps)."""
+    pytest.importorskip("scipy")
+    r, sig, dl, K = 0.05, 0.3, 0.25, 0.05
+    lm = inputs.lmm_flat(n_fwd=6, vol=sig, rate=r, delta=dl, scheme=1)
+    h, sh = dl, math.sqrt(dl)
+    L0 = r
+    a0 = dl * L0 / (1 + dl * L0)
+
+    def L1(z0):                      # forward 1 after step 0 (alive: forwards 1.., prefix a_1)
+        return L0 * (1.0 + sig * sig * a0 * h + sig * sh * z0)
+
+    def L2_after0(z0):               # forward 2 after step 0 (prefix a_1 + a_2)
+        return L0 * (1.0 + sig * sig * 2 * a0 * h + sig * sh * z0)
+
+    zk1 = (K / L0 - 1.0 - sig * sig * a0 * h) / (sig * sh)
+    cap1 = _quad_kinked(lambda z: dl * max(L1(z) - K, 0.0) / ((1 + dl * r) * (1 + dl * L1(z))), zk1)
+
+    xs, ws = np.polynomial.hermite_e.hermegauss(120)
+    ws = ws / math.sqrt(2 * math.pi)
+    cap2 = 0.0
+    for z0, w0 in zip(xs, ws):
+        l1, l2 = L1(z0), L2_after0(z0)
+        a = dl * l2 / (1 + dl * l2)
+        g = lambda z1: l2 * (1.0 + sig * sig * a * h + sig * sh * z1)
+        zk = (K / l2 - 1.0 - sig * sig * a * h) / (sig * sh)
+        f = lambda z1: dl * max(g(z1) - K, 0.0) / ((1 + dl * r) * (1 + dl * l1) * (1 + dl * g(z1)))
+        cap2 += w0 * _quad_kinked(f, zk)
+
+    for seq in (O.SOBOL_DS, O.RASRAP):
+        q = O.Sequence(seq, 6, 16, 3, joe_kuo=JK)
+        theta = O.lmm_caplets(q, lm, [K], 8192)
+        rq, sd = O.rq_stats(theta)
+        assert abs(rq[0] - cap1) <= 4 * sd[0] / 4 + 1e-9 * cap1, (rq[0], cap1, sd[0])
+        assert abs(rq[1] - cap2) <= 4 * sd[1] / 4 + 1e-9 * cap2, (rq[1], cap2, sd[1])
+    # and the scheme is not log-Euler: the two discretizations differ by more than the noise
+    q = O.Sequence(O.SOBOL_DS, 6, 16, 3, joe_kuo=JK)
+    le = O.rq_stats(O.lmm_caplets(q, dict(lm, scheme=0), [K], 8192))
+    eu = O.rq_stats(O.lmm_caplets(q, lm, [K], 8192))
+    assert abs(le[0][1] - eu[0][1]) > 10 * (le[1][1] + eu[1][1]) / 4
+
+
 def test_lmm_black_formula_within_discretization_budget():
     # Black caplet (read with delta in front, as eq. black_cap must be), spot-measure
     # log-Euler bias measured by halving the step (Richardson): |P_h - P_{h/2}| ~ bias / 2.

@@ -72,7 +72,7 @@ def test_noalloc_refuses_what_price_caplets_refuses_with_the_same_codes():
     out = torch.empty(64 * 200 * 8, dtype=torch.float64, device="cuda")
     K = np.array([0.05])
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    cases = [(inputs.lmm_two_factor(8, seed=1), 2), (dict(inputs.lmm_flat(8), scheme=1), 2),
+    cases = [(inputs.lmm_two_factor(8, seed=1), 2), (dict(inputs.lmm_flat(8), scheme=2), 2),
              (inputs.lmm_flat(161), 2), (inputs.lmm_flat(8), 0)]
     for lm, M in cases:
         keep: list = []
