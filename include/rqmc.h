@@ -91,9 +91,11 @@ typedef struct {
     int n_fwd;               /* nf >= 1 */
     int n_factors;           /* d in {1, 2} */
     int scheme;              /* rqmc_lmm_scheme */
-    int reserved;
+    int init;                /* what L0 points to: 0 = forwards, 1 = bond prices (see L0) */
     double delta;            /* accrual period = time step, > 0 */
-    const double *L0;        /* [nf+1]: L_0(0), L_1(0), ..., L_nf(0) (eq. BL from bond prices) */
+    const double *L0;        /* init 0: [nf+1] forwards L_0(0), L_1(0), ..., L_nf(0);
+                              * init 1: [nf+2] bond prices B_0(0), ..., B_{nf+1}(0) > 0, converted
+                              * by eq. BL, L_n(0) = (B_n(0) - B_{n+1}(0)) / (delta B_{n+1}(0)) */
     const double *vol;       /* [nf]: |sigma_n|, n = 1..nf */
     const double *loadings;  /* [nf][d] unit rows b_n; may be NULL when d == 1 */
 } rqmc_lmm_params;

@@ -163,6 +163,29 @@ void fill_lmm(LmmModel<T> &md, const rqmc_lmm_params *p, const double *K, int nK
 template void fill_lmm<float>(LmmModel<float> &, const rqmc_lmm_params *, const double *, int, int);
 template void fill_lmm<double>(LmmModel<double> &, const rqmc_lmm_params *, const double *, int, int);
 
+rqmc_status lmm_curve(const rqmc_lmm_params *in, LmmCurve &c) {
+    if (!in) { set_error("LMM parameters missing"); return RQMC_EINVAL; }
+    c.p = *in;
+    c.L0.clear();
+    if (in->init == 0) return RQMC_OK;
+    if (in->init != 1) { set_error("init must be 0 (forwards) or 1 (bond prices)"); return RQMC_EINVAL; }
+    if (!in->L0 || in->n_fwd < 1 || in->n_fwd > kMaxFwd || !(in->delta > 0.0) || !std::isfinite(in->delta)) {
+        set_error("bond prices need n_fwd in 1..160, delta > 0 and nf + 2 prices");
+        return RQMC_EINVAL;
+    }
+    const int nf = in->n_fwd;
+    for (int n = 0; n < nf + 2; ++n)
+        if (!(in->L0[n] > 0.0) || !std::isfinite(in->L0[n])) {
+            set_error("bond prices must be positive and finite");
+            return RQMC_EINVAL;
+        }
+    c.L0.resize(nf + 1);
+    for (int n = 0; n <= nf; ++n) c.L0[n] = (in->L0[n] - in->L0[n + 1]) / (in->delta * in->L0[n + 1]);   // eq. BL
+    c.p.L0 = c.L0.data();
+    c.p.init = 0;
+    return RQMC_OK;
+}
+
 rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool adjoint) {
     if (!p || !p->L0 || !p->vol) { set_error("LMM parameters missing"); return RQMC_EINVAL; }
     if (p->n_fwd < 1 || p->n_fwd > kMaxFwd) { set_error("n_fwd must be in 1..160"); return RQMC_EINVAL; }
@@ -276,7 +299,11 @@ extern "C" rqmc_status rqmc_plan_product(int s, int64_t N, int64_t offset, int M
 extern "C" rqmc_status rqmc_plan_caplets(const rqmc_lmm_params *p, const double *strikes_host, int n_strikes,
                                          int64_t N, int64_t offset, int M, rqmc_sequence seq, uint64_t seed,
                                          rqmc_precision prec, rqmc_plan **plan) {
-    rqmc_status rs = check_lmm(p, strikes_host, n_strikes, false);
+    LmmCurve curve;
+    rqmc_status rs = lmm_curve(p, curve);
+    if (rs != RQMC_OK) return rs;
+    p = &curve.p;
+    rs = check_lmm(p, strikes_host, n_strikes, false);
     if (rs != RQMC_OK) return rs;
     rqmc_plan *pl = nullptr;
     rs = new_plan(kCaplets, p->n_fwd * p->n_factors, N, offset, M, seq, seed, prec, &pl);
@@ -520,7 +547,11 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
                                          const double *weights_host, int64_t N, int64_t offset, int M,
                                          rqmc_sequence seq, uint64_t seed, rqmc_precision prec, int checkpoint,
                                          rqmc_plan **plan) {
-    rqmc_status rs = check_lmm(p, strikes_host, n_strikes, true);
+    LmmCurve curve;
+    rqmc_status rs = lmm_curve(p, curve);
+    if (rs != RQMC_OK) return rs;
+    p = &curve.p;
+    rs = check_lmm(p, strikes_host, n_strikes, true);
     if (rs != RQMC_OK) return rs;
     if (p->n_fwd > kMaxAdjFwd) { set_error("adjoint: n_fwd must be <= 80"); return RQMC_EUNSUPPORTED; }
     if (prec != RQMC_FP32) { set_error("adjoint: FP32 paths only"); return RQMC_EUNSUPPORTED; }

@@ -75,7 +75,11 @@ extern "C" rqmc_status rqmc_price_caplets_noalloc(const rqmc_lmm_params *p, cons
         set_error("rqmc_price_caplets_noalloc: theta_dev is required");
         return RQMC_EINVAL;
     }
-    rqmc_status rs = check_lmm(p, strikes_host, n_strikes, false);
+    LmmCurve curve;
+    rqmc_status rs = lmm_curve(p, curve);
+    if (rs != RQMC_OK) return rs;
+    p = &curve.p;
+    rs = check_lmm(p, strikes_host, n_strikes, false);
     if (rs != RQMC_OK) return rs;
     if ((rs = common_checks(p->n_fwd * p->n_factors, N, 0, M, seq, prec)) != RQMC_OK) return rs;
 

@@ -207,6 +207,13 @@ int adjoint_grid(const Plan &pl);
 constexpr int kAdjointThreads = 256;   // CTA size of the adjoint kernel
 int occupancy_blocks(const Plan &pl);
 
+// ---- the caller's initial curve as forwards (eq. BL for bond prices); p points into itself
+struct LmmCurve {
+    rqmc_lmm_params p;
+    std::vector<double> L0;
+};
+rqmc_status lmm_curve(const rqmc_lmm_params *in, LmmCurve &c);
+
 // ---- argument checks and model constants shared by the caplet entry points (api.cu)
 rqmc_status common_checks(int s, int64_t N, int64_t offset, int M, int seq, int prec);
 rqmc_status check_lmm(const rqmc_lmm_params *p, const double *K, int nK, bool adjoint);

@@ -44,7 +44,7 @@ class RqmcError(RuntimeError):
 
 
 class LmmParams(C.Structure):
-    _fields_ = [("n_fwd", C.c_int), ("n_factors", C.c_int), ("scheme", C.c_int), ("reserved", C.c_int),
+    _fields_ = [("n_fwd", C.c_int), ("n_factors", C.c_int), ("scheme", C.c_int), ("init", C.c_int),
                 ("delta", C.c_double), ("L0", C.POINTER(C.c_double)), ("vol", C.POINTER(C.c_double)),
                 ("loadings", C.POINTER(C.c_double))]
 
@@ -148,11 +148,14 @@ def _stream(stream):
 
 
 def _lmm_struct(lmm: dict, keep: list) -> LmmParams:
-    L0 = np.ascontiguousarray(lmm["L0"], dtype=np.float64)
+    """The model dict as rqmc_lmm_params: the initial curve is "B0" (bond prices B_0..B_nf+1,
+    converted by the library with eq. BL) when present, else "L0" (forwards L_0..L_nf)."""
+    bonds = lmm.get("B0") is not None
+    L0 = np.ascontiguousarray(lmm["B0"] if bonds else lmm["L0"], dtype=np.float64)
     vol = np.ascontiguousarray(lmm["vol"], dtype=np.float64)
     keep += [L0, vol]
-    st = LmmParams(int(lmm["n_fwd"]), int(lmm.get("d", 1)), int(lmm.get("scheme", 0)), 0, float(lmm["delta"]),
-                   _dp(L0), _dp(vol), None)
+    st = LmmParams(int(lmm["n_fwd"]), int(lmm.get("d", 1)), int(lmm.get("scheme", 0)), 1 if bonds else 0,
+                   float(lmm["delta"]), _dp(L0), _dp(vol), None)
     if lmm.get("loadings") is not None:
         ld = np.ascontiguousarray(lmm["loadings"], dtype=np.float64)
         keep.append(ld)

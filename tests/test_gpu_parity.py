@@ -207,6 +207,32 @@ def test_caplets_euler_zero_volatility_and_refusals(R):
     assert e.value.status == 1
 
 
+def test_caplets_from_bond_prices(R):
+    """The initial curve given as bond prices B_0(0)..B_nf+1(0) (rqmc_lmm_params.init = 1): the
+    library's eq. BL conversion gives the forwards the inputs module computes, so caplets and
+    Greeks are bit-identical to the forwards-given call, and match the oracle."""
+    st = inputs.TREASURY_STUDY
+    B = inputs.treasury_bonds(11, st["delta"])
+    lm_f = inputs.lmm_from_bonds(B, st["delta"], st["vol"])
+    lm_b = dict(lm_f, B0=B)
+    K = np.array([st["K"]])
+    for prec in ("fp64", "fp32"):
+        a, _, _ = R.price_caplets(lm_f, K, 2048, 3, "sobol_ds", 4, prec=prec)
+        b, _, _ = R.price_caplets(lm_b, K, 2048, 3, "sobol_ds", 4, prec=prec)
+        assert np.array_equal(a, b), prec
+    th_o = O.lmm_caplets(O.Sequence(O.SOBOL_DS, 10, 3, 4, joe_kuo=JK), lm_f, K, 2048)
+    np.testing.assert_allclose(b, th_o, rtol=1e-4, atol=1e-9)
+    w = np.ones(10)
+    ga = R.price_adjoint(lm_f, K, w, 1024, 2, "philox", 4)
+    gb = R.price_adjoint(lm_b, K, w, 1024, 2, "philox", 4)
+    for x, y in zip(ga, gb):
+        assert np.array_equal(x, y)
+    bad = dict(lm_b, B0=np.concatenate([B[:5], [-1.0], B[6:]]))
+    with pytest.raises(R.RqmcError) as e:
+        R.price_caplets(bad, K, 64, 1, "philox", 1)
+    assert e.value.status == 1
+
+
 # ------------------------------------------------------------------ MBS
 @pytest.mark.parametrize("seq", [O.RASRAP, O.SOBOL_DS, O.PHILOX, O.HALTON_RS, O.SOBOL_LMS])
 def test_mbs_small(R, seq):
