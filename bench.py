@@ -511,7 +511,7 @@ def other_workloads(args, dev, seed, pk):
         o = torch.empty(p.output_size(), dtype=torch.float64, device=dev)
         ms = _time_plan(lambda: p.execute(o), 1, flush)
         parts = p.split_batch(o.cpu().numpy())
-        imb = p.batch_imbalance() if hasattr(p, "batch_imbalance") else None
+        bstats = p.batch_stats()   # of the last timed execute
         p.close()
         steps = sum(d["N"] * Mb * (d["n_fwd"] if d["kind"] == "lmm" else d["months"]) for d in desc)
         slots = fma = 0.0
@@ -540,7 +540,7 @@ def other_workloads(args, dev, seed, pk):
         o_steps = sum(desc[i]["N"] * (desc[i]["n_fwd"] if desc[i]["kind"] == "lmm" else desc[i]["months"]) for i in sample)
         out["batch_512_M32_fp32_sobol"] = {
             "ms": ms, "path_steps_per_s": steps / (ms / 1e3), "path_steps": steps,
-            "imbalance_max_sm_busy_over_mean": imb,
+            "imbalance_max_sm_busy_over_mean": bstats["imbalance"], "class_spans_ms": bstats,
             "parity": {"ok": rel <= 1e-4, "tol": 1e-4, "max_rel_err": rel,
                        "checked": f"{len(sample)} instruments (every 32nd), replication 0, full N"},
             "cpu_baseline": {"value": o_steps / t_o, "unit": "path-steps/s", "cores": T, "kind": "oracle",

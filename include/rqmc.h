@@ -242,6 +242,12 @@ rqmc_status rqmc_plan_points(int s, int64_t N, int64_t offset, int M, rqmc_seque
  * replication [value, dV/dL_n(0) (nf), dV/dvol_n (nf), unweighted caplet values (nf*n_strikes)];
  * with all weights zero they skip the reverse sweep and act as a d-factor caplet pricer. */
 int64_t rqmc_plan_output_size(const rqmc_plan *plan);
+/* Timing of the last execute of a batch plan (not in the paper), from per-CTA records of its
+ * persistent kernels (global timer): an SM counts as busy from the first start to the last end
+ * of the CTAs it ran.  out_host[0] = busiest SM / mean SM (1 = perfectly balanced), [1] = span of
+ * all CTAs in ms, [2], [3], [4] = span of the 160-forward, MBS and smaller-strip classes in ms
+ * (0 when empty).  Synchronous (one copy); n must be at least 5; EINVAL for other plans. */
+rqmc_status rqmc_plan_batch_stats(rqmc_plan *plan, double *out_host, int n);
 /* Kernel launches one execute performs (for launch accounting). */
 int rqmc_plan_launches(const rqmc_plan *plan);
 /* Tuning knobs of a plan: threads per block and paths per thread (0 = keep). */

@@ -148,6 +148,11 @@ static rqmc_status setup_launch(BatchPlan &bp, int threads, int ppt, bool cap_n)
     size_t o_items[kBatchClasses];
     for (int k = 0; k < kBatchClasses; ++k) o_items[k] = cv.take(sizeof(BatchItem) * std::max<size_t>(items[k].size(), 1));
     const size_t o_cnt = cv.take(sizeof(uint32_t) * 4);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const uint32_t stats_cap = 8u * (uint32_t)std::max(sms, 1);   // at most 8 CTAs of 256 threads per SM
+    const size_t o_stats = cv.take(sizeof(unsigned long long) * 3 * kBatchClasses * stats_cap);
     const size_t o_part = cv.take(sizeof(double) * part);
     const size_t o_theta = cv.take(sizeof(double) * theta);
     cudaError_t e = cudaMalloc(&bp.d_work, cv.off);
@@ -171,6 +176,8 @@ static rqmc_status setup_launch(BatchPlan &bp, int threads, int ppt, bool cap_n)
     }
     bl.n_inst = (uint32_t)insts.size();
     bl.counter = reinterpret_cast<uint32_t *>(d + o_cnt);
+    bl.stats = reinterpret_cast<unsigned long long *>(d + o_stats);
+    bl.stats_cap = stats_cap;
     bl.partials = reinterpret_cast<double *>(d + o_part);
     bl.theta = reinterpret_cast<double *>(d + o_theta);
     bl.threads = threads;
@@ -470,3 +477,49 @@ void batch_destroy(Plan &pl) {
 int batch_ppt(const Plan &pl) { return pl.batch ? pl.batch->bl.ppt : 0; }
 
 }  // namespace rqmc
+
+using namespace rqmc;
+
+// Timing of the last execute of a batch plan, from the CTA records of its persistent kernels
+// (synchronises: one device-to-host copy).  An SM is busy from the first start to the last
+// end of the CTAs it ran; out[0] = busiest SM / mean SM, out[1] = the span of all CTAs in ms,
+// out[2..4] = the span of each work class in ms (0 when the class is empty).
+extern "C" rqmc_status rqmc_plan_batch_stats(rqmc_plan *plan, double *out_host, int n) {
+    if (!plan || !out_host || n < 5 || plan->kind != kBatch || !plan->batch) {
+        set_error("rqmc_plan_batch_stats: a batch plan and 5 output values are required");
+        return RQMC_EINVAL;
+    }
+    const BatchLaunch &bl = plan->batch->bl;
+    std::vector<unsigned long long> h(3ull * kBatchClasses * bl.stats_cap);
+    const cudaError_t e = cudaMemcpy(h.data(), bl.stats, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_error(std::string("rqmc_plan_batch_stats: ") + cudaGetErrorString(e));
+        return RQMC_ECUDA;
+    }
+    std::map<unsigned long long, std::pair<unsigned long long, unsigned long long>> sm;   // SM -> (first start, last end)
+    unsigned long long lo = ~0ull, hi = 0;
+    for (int k = 0; k < kBatchClasses; ++k) {
+        unsigned long long klo = ~0ull, khi = 0;
+        for (uint32_t b = 0; b < bl.stats_cap; ++b) {
+            const unsigned long long *r = h.data() + 3ull * ((unsigned long long)k * bl.stats_cap + b);
+            if (r[2] == 0) continue;   // no record: CTA not launched
+            auto it = sm.find(r[0]);
+            if (it == sm.end()) sm[r[0]] = {r[1], r[2]};
+            else it->second = {std::min(it->second.first, r[1]), std::max(it->second.second, r[2])};
+            klo = std::min(klo, r[1]);
+            khi = std::max(khi, r[2]);
+        }
+        out_host[2 + k] = khi > klo ? (double)(khi - klo) * 1e-6 : 0.0;
+        lo = std::min(lo, klo);
+        hi = std::max(hi, khi);
+    }
+    double busy_max = 0.0, busy_sum = 0.0;
+    for (const auto &kv : sm) {
+        const double b = (double)(kv.second.second - kv.second.first);
+        busy_max = std::max(busy_max, b);
+        busy_sum += b;
+    }
+    out_host[0] = sm.empty() || busy_sum <= 0.0 ? 0.0 : busy_max / (busy_sum / (double)sm.size());
+    out_host[1] = hi > lo ? (double)(hi - lo) * 1e-6 : 0.0;
+    return RQMC_OK;
+}

@@ -27,6 +27,9 @@ __global__ void batch_theta_kernel(const BatchInst *__restrict__ insts, const do
 cudaError_t launch_batch(const BatchLaunch &bl, int seq, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(bl.counter, 0, kBatchClasses * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bl.stats, 0, sizeof(unsigned long long) * 3 * kBatchClasses * bl.stats_cap, st)) !=
+        cudaSuccess)
+        return e;
     bool forked[kBatchClasses] = {};
     if ((e = cudaEventRecord(bl.fork, st)) != cudaSuccess) return e;
     for (int k = 1; k < kBatchClasses; ++k) {

@@ -102,13 +102,27 @@ __device__ __forceinline__ void batch_mbs(const BatchInst &bi, const BatchItem &
 }
 
 // One persistent kernel per work class KIND (see BatchLaunch).
+// CTA timing record: SM id, global-timer start and end of the CTA's item loop.
+__device__ __forceinline__ unsigned long long batch_clock() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ uint32_t batch_smid() {
+    uint32_t id;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+    return id;
+}
+
 template <int SEQ, int KIND>
 __global__ void __launch_bounds__(256, KIND == 0 ? 1 : KIND == 1 ? 4 : 2) batch_kernel(const BatchInst *__restrict__ insts,
                                                                     const BatchItem *__restrict__ items,
                                                                     uint32_t n_items, uint32_t *counter,
-                                                                    double *partials, int ppt) {
+                                                                    double *partials, int ppt,
+                                                                    unsigned long long *stats, uint32_t stats_cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ uint32_t s_ticket;
+    const unsigned long long t_start = batch_clock();
     for (;;) {
         if (threadIdx.x == 0) s_ticket = atomicAdd(counter, 1u);
         __syncthreads();
@@ -140,6 +154,12 @@ __global__ void __launch_bounds__(256, KIND == 0 ? 1 : KIND == 1 ? 4 : 2) batch_
             batch_mbs<SEQ>(bi, it, gv, r, smem_raw);
         }
     }
+    if (threadIdx.x == 0 && stats && blockIdx.x < stats_cap) {
+        unsigned long long *rec = stats + 3ull * ((unsigned long long)KIND * stats_cap + blockIdx.x);
+        rec[0] = batch_smid();
+        rec[1] = t_start;
+        rec[2] = batch_clock();
+    }
 }
 
 template <int SEQ, int KIND>
@@ -157,7 +177,7 @@ cudaError_t launch_batch_class(const BatchLaunch &bl, cudaStream_t st) {
     if (occ < 1) occ = 1;
     const unsigned grid = (unsigned)std::min<unsigned long long>(bl.n_items[KIND], (unsigned long long)occ * sms);
     kern<<<grid, bl.threads, smem, st>>>(bl.insts, bl.items[KIND], bl.n_items[KIND], bl.counter + KIND, bl.partials,
-                                         bl.ppt);
+                                         bl.ppt, bl.stats, bl.stats_cap);
     return cudaGetLastError();
 }
 

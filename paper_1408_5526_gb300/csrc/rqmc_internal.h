@@ -124,6 +124,8 @@ struct BatchLaunch {
     uint32_t n_items[kBatchClasses], n_inst;
     uint32_t *counter;            // [kBatchClasses] ticket counters
     double *partials, *theta;
+    unsigned long long *stats;    // [kBatchClasses][stats_cap] CTA records: SM id, start, end (ns)
+    uint32_t stats_cap;
     int threads, ppt;
     size_t smem[kBatchClasses];
     cudaStream_t side[kBatchClasses - 1];   // classes 1.. run on forked streams

@@ -34,7 +34,7 @@ EXPORTS = ["rqmc_set_sobol_table", "rqmc_points", "rqmc_integrate_product", "pri
            "rqmc_plan_adjoint", "rqmc_plan_batch", "rqmc_plan_output_size", "rqmc_plan_launches",
            "rqmc_plan_set_launch", "rqmc_plan_execute", "rqmc_plan_check", "rqmc_plan_destroy",
            "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version", "rqmc_price_caplets_noalloc",
-           "rqmc_plan_points", "rqmc_probe_pipes"]
+           "rqmc_plan_points", "rqmc_probe_pipes", "rqmc_plan_batch_stats"]
 
 
 class RqmcError(RuntimeError):
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         L.rqmc_plan_batch.argtypes = [C.POINTER(Instrument), C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, pp]
         L.rqmc_plan_points.argtypes = [C.c_int, i64, i64, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_int, pp]
         L.rqmc_probe_pipes.argtypes = [dp, C.c_int]
+        L.rqmc_plan_batch_stats.argtypes = [vp, dp, C.c_int]
         L.rqmc_plan_output_size.argtypes = [vp]
         L.rqmc_plan_output_size.restype = i64
         L.rqmc_plan_launches.argtypes = [vp]
@@ -373,6 +374,18 @@ class Plan:
         pl = cls(h, M, 0)
         pl.insts = list(insts)
         return pl
+
+    def batch_stats(self) -> dict:
+        """Timing of the last execute of a batch plan: busiest SM / mean SM, span of all CTAs and
+        of each work class (ms)."""
+        L = load()
+        r = np.zeros(5)
+        _check(L, L.rqmc_plan_batch_stats(self._h, _dp(r), 5))
+        return {"imbalance": float(r[0]), "span_ms": float(r[1]), "class_160_ms": float(r[2]),
+                "class_mbs_ms": float(r[3]), "class_small_ms": float(r[4])}
+
+    def batch_imbalance(self) -> float:
+        return self.batch_stats()["imbalance"]
 
     def split_batch(self, theta):
         return _split_batch(theta.cpu().numpy() if hasattr(theta, "cpu") else theta, self.insts, self.M)

@@ -101,3 +101,16 @@ def test_batch_512_instrument_draw_with_capped_N(R, seq, M):
     ref = _oracle(seq, M, 1, insts)
     worst = max(float(np.max(np.abs(g - r) / np.abs(r))) for g, r in zip(got, ref))
     assert worst <= 1e-4, worst
+
+
+def test_batch_stats_report_the_load_balance(R):
+    """The per-CTA timing records of the persistent kernels: the busiest SM over the mean SM
+    is at least 1, every non-empty work class has a positive span within the whole span, and
+    an empty class reports 0."""
+    p = R.Plan.batch([INSTS[k] for k in (0, 1, 2, 3)], 3, O.SOBOL_DS, 5)   # no strip beyond 80 forwards
+    p.execute()
+    st = p.batch_stats()
+    p.close()
+    assert st["imbalance"] >= 1.0 and st["span_ms"] > 0.0
+    assert st["class_160_ms"] == 0.0
+    assert 0.0 < st["class_mbs_ms"] <= st["span_ms"] * 1.0001 and 0.0 < st["class_small_ms"] <= st["span_ms"] * 1.0001
