@@ -22,7 +22,8 @@
 // and at the fixing of forward n (Y = its post-step X, L = 2^Y / delta, G_n = sum_{m>=n} P_m)
 //     Xb_n       += ln 2 [sum_k w_{n,k} delta 1{L > K_k} D_n L - a(Y) G_n].
 // The adjoints Xb live in per-thread global columns (16-byte chunks, loaded two chunks ahead;
-// the columns stay in L2), the vega accumulators likewise, updated by vector reductions that
+// the columns stay in L2; the two top chunks, first in every step, stay in registers across
+// steps), the vega accumulators likewise, updated by vector reductions that
 // the thread does not wait for.  The normals of a step are regenerated from the counter, never
 // stored.  At the end dV/dL_n(0) = Xb_n / (L_n(0) ln 2) and dV/dvol_n = sum over steps of
 // sigma_bar_n . b_n.  Per-thread value / delta / vega / price accumulators sit in global
@@ -176,18 +177,17 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
             // the adjoints accumulate in the thread's global columns
             for (int c = 0; c < nch; ++c) xb4[(size_t)c * T] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
             float Dcur = disc, G = 0.0f;
+            // the two top chunks (nch-1, nch-2) are processed first in every step: their values
+            // carry over in registers; the others are loaded two chunks ahead from the columns
+            float4 top0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), top1 = top0;
+            float2 At_next = md.reverse ? rec[(size_t)(nf - 1) * T] : make_float2(0.0f, 0.0f);
             for (int t = md.reverse ? nf - 1 : -1; t >= 0; --t) {
                 const int c0 = t >> 2, jt = t & 3;
-                const float2 At = rec[(size_t)t * T];
-                // software pipeline over the adjoint chunks nch-1 .. c0, loaded two ahead
-                const float4 *q = xb4 + (size_t)(nch - 1) * T;
-                float4 p0 = *q;
-                q -= T;
-                float4 p1 = p0;
-                if (nch - 2 >= c0) {
-                    p1 = *q;
-                    q -= T;
-                }
+                const float2 At = At_next;
+                if (t > 0) At_next = rec[(size_t)(t - 1) * T];   // one step ahead
+                const float4 *q = xb4 + (ptrdiff_t)(nch - 3) * (ptrdiff_t)T;   // chunk nch-3 (read only when it exists)
+                float4 p0 = top0;
+                float4 p1 = nch - 2 >= c0 ? top1 : top0;
                 float Z0, Z1 = 0.0f;
                 if constexpr (D == 2) normals32_two_dims<SEQ>(pg, 2 * t, 2 * t + 1, Z0, Z1);
                 else Z0 = Draw<float>::normal(pg, t);
@@ -251,7 +251,10 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                             Xb[j] = fmaf(S, inv_h * fmaf(-a, a, a), Xb[j]);   // + h (sigma.B) a (1 - a)
                         }
                     }
-                    xb4[(size_t)c * T] = make_float4(Xb[0], Xb[1], Xb[2], Xb[3]);
+                    const float4 nv = make_float4(Xb[0], Xb[1], Xb[2], Xb[3]);
+                    xb4[(size_t)c * T] = nv;
+                    if (c == nch - 1) top0 = nv;
+                    if (c == nch - 2) top1 = nv;
                     red_add_v4(vg, vv);
                     vg -= T;
                 };
