@@ -158,6 +158,30 @@ __device__ __forceinline__ uint32_t halton_high(const HaltonDim &h, const uint16
     return r;
 }
 
+// halton_high of q (into *r0) and of q + 1 modulo p^(L-1) (into *r1) from one pass over the
+// digits of q: the digits of q + 1 are those of q with a carry that runs through the low digits
+// equal to p - 1.
+__device__ __forceinline__ void halton_high2(const HaltonDim &h, const uint16_t *__restrict__ sg, uint32_t q,
+                                             uint32_t *r0, uint32_t *r1) {
+    uint32_t a = 0, b = 0, cy = 1;
+    for (uint32_t k = 1; k < h.L; ++k) {
+        uint32_t qq = __umulhi(q, h.magic);
+        uint32_t d = q - qq * h.p;
+        if ((int32_t)d < 0) {
+            d += h.p;
+            qq -= 1;
+        }
+        uint32_t e = d + cy;
+        cy = e == h.p ? 1u : 0u;
+        e = cy ? 0u : e;
+        a = a * h.p + (uint32_t)sg[d];
+        b = b * h.p + (uint32_t)sg[e];
+        q = qq;
+    }
+    *r0 = a;
+    *r1 = b;
+}
+
 template <typename T>
 __device__ __forceinline__ void store_run(T *dst, const T (&v)[kRun]) {
     if constexpr (sizeof(T) == 4) {
@@ -198,25 +222,20 @@ __device__ __forceinline__ void run_from_u32(const uint32_t (&x)[kRun], T (&v)[k
 struct HaltonRow {
     unsigned long long P, S0, S1;
     double invD;
-    uint32_t pL;
+    uint32_t pL, thr0, thr1;   // halton_lower(h, R, c) is R < thr_c
     float inv_pL, a0, a1, b0, b1;
     __device__ __forceinline__ explicit HaltonRow(const HaltonDim &h)
-        : P(h.P), S0(h.S[0]), S1(h.S[1]), invD(h.invD), pL(h.pL), inv_pL(h.inv_pL), a0(h.a[0]), a1(h.a[1]),
-          b0(h.b[0]), b1(h.b[1]) {}
+        : P(h.P), S0(h.S[0]), S1(h.S[1]), invD(h.invD), pL(h.pL), thr0((h.pL >> 1) + (h.tie & 1u)),
+          thr1((h.pL >> 1) + ((h.tie >> 1) & 1u)), inv_pL(h.inv_pL), a0(h.a[0]), a1(h.a[1]), b0(h.b[0]), b1(h.b[1]) {}
     __device__ __forceinline__ unsigned long long num(uint32_t R, uint32_t c) const {
         return (unsigned long long)R * P + (c ? S1 : S0);
     }
     // the values of unif32_halton / unif64_halton
-    __device__ __forceinline__ bool lower(uint32_t R, uint32_t c) const {
-        const uint32_t Rc = pL - 1u - R;
-        if (R != Rc) return R < Rc;
-        const unsigned long long S = c ? S1 : S0;
-        return S <= P - 1ull - S;
-    }
     __device__ __forceinline__ Unif32 unif32(uint32_t R, uint32_t c) const {
-        const bool lo = lower(R, c);
-        const float q = lo ? fmaf((float)R, inv_pL, c ? a1 : a0) : fmaf((float)(pL - 1u - R), inv_pL, c ? b1 : b0);
-        return Unif32{q, lo};
+        const bool lo = R < (c ? thr1 : thr0);
+        const uint32_t Rs = lo ? R : pL - 1u - R;
+        const float off = c ? (lo ? a1 : b1) : (lo ? a0 : b0);
+        return Unif32{fmaf((float)Rs, inv_pL, off), lo};
     }
     __device__ __forceinline__ Unif64 unif64(uint32_t R, uint32_t c) const {
         const unsigned long long n = num(R, c);
@@ -313,12 +332,17 @@ __global__ void __launch_bounds__(256) points_run_kernel(const GenParams g, uint
                         d0 += h.p;
                         q0 -= 1;
                     }
-                    uint32_t q1 = q0 + 1, c1 = c0;
-                    if (q1 == pLm1) {   // the run reaches p^L: the low part wraps into the carry
-                        q1 = 0;
-                        c1 = 1;
+                    // the run reaches p^L: the low part wraps into the carry (and q0 + 1 to 0)
+                    const uint32_t c1 = q0 + 1 == pLm1 ? 1u : c0;
+                    // R'(q0 + 1) only where some lane's run wraps its lowest digit: always for
+                    // small p, in about 256/p of the warps for p > 256
+                    uint32_t R0, R1;
+                    if (__any_sync(0xffffffffu, d0 + (kRun - 1) >= h.p)) {
+                        halton_high2(h, sg, q0, &R0, &R1);
+                    } else {
+                        R0 = halton_high(h, sg, q0);
+                        R1 = R0;
                     }
-                    const uint32_t R0 = halton_high(h, sg, q0), R1 = halton_high(h, sg, q1);
 #pragma unroll
                     for (int k = 0; k < kRun; ++k) {
                         uint32_t d = d0 + k;

@@ -95,7 +95,8 @@ struct __align__(16) HaltonDim {
     float inv_pL;            // FP32 conversion: u = R / p^L + (S[c] + 1/2) / D
     float a[2];              // (S[c] + 1/2) / D
     float b[2];              // (P - 1 - S[c] + 1/2) / D, the complement's tail
-    float pad_;
+    uint32_t tie;            // bit c: p^L odd and 2 S[c] <= P - 1, i.e. the middle R = (p^L - 1)/2
+                             // puts num = R P + S[c] in the lower half (see halton_lower)
 };
 
 struct GenParams {
@@ -246,12 +247,11 @@ __device__ __forceinline__ unsigned long long halton_num(const HaltonDim &h, uin
     return (unsigned long long)R * h.P + h.S[c];
 }
 
-// u <= 1/2 side test, exact: num <= D-1-num.
+// u <= 1/2 side test, exact: num <= D-1-num, i.e. 2 (R P + S[c]) <= p^L P - 1.  That holds
+// for every 2R <= p^L - 2 (as S[c] <= P - 1), for no 2R >= p^L, and for 2R = p^L - 1 exactly
+// when 2 S[c] <= P - 1; so it is R < floor(p^L / 2) + (bit c of tie).
 __device__ __forceinline__ bool halton_lower(const HaltonDim &h, uint32_t R, uint32_t c) {
-    const uint32_t Rc = h.pL - 1u - R;
-    if (R != Rc) return R < Rc;
-    const unsigned long long S = h.S[c];
-    return S <= h.P - 1ull - S;
+    return R < (h.pL >> 1) + ((h.tie >> c) & 1u);
 }
 
 // ------------------------------------------------------------------ Sobol'
@@ -287,8 +287,8 @@ __device__ __forceinline__ Unif64 unif64_from_u32(uint32_t x) {
 }
 __device__ __forceinline__ Unif32 unif32_halton(const HaltonDim &h, uint32_t R, uint32_t c) {
     const bool lower = halton_lower(h, R, c);
-    const float q = lower ? fmaf((float)R, h.inv_pL, h.a[c]) : fmaf((float)(h.pL - 1u - R), h.inv_pL, h.b[c]);
-    return Unif32{q, lower};
+    const uint32_t Rs = lower ? R : h.pL - 1u - R;
+    return Unif32{fmaf((float)Rs, h.inv_pL, lower ? h.a[c] : h.b[c]), lower};
 }
 __device__ __forceinline__ Unif64 unif64_halton(const HaltonDim &h, uint32_t R, uint32_t c) {
     const unsigned long long num = halton_num(h, R, c);

@@ -156,7 +156,9 @@ __global__ void setup_halton_kernel(const BaseConst *__restrict__ bases, int s, 
         h.a[c] = (float)(((double)h.S[c] + 0.5) * b.invD);
         h.b[c] = (float)(((double)(b.P - 1ull - h.S[c]) + 0.5) * b.invD);
     }
-    h.pad_ = 0.f;
+    h.tie = 0;
+    for (int c = 0; c < 2; ++c)
+        if ((b.pL & 1u) && h.S[c] <= b.P - 1ull - h.S[c]) h.tie |= 1u << c;
     hdim[idx] = h;
     if (!(ok && ok0)) atomicOr(status, 1u);
     (void)ok1;   // the carry case is reached only by points the range check admits
