@@ -182,16 +182,17 @@ __device__ __forceinline__ void halton_high2(const HaltonDim &h, const uint16_t 
     *r1 = b;
 }
 
-template <typename T>
-__device__ __forceinline__ void store_run(T *dst, const T (&v)[kRun]) {
+template <typename T, int RUN = kRun>
+__device__ __forceinline__ void store_run(T *dst, const T (&v)[RUN]) {
+    static_assert(RUN % 4 == 0, "runs of whole 16-byte stores");
     if constexpr (sizeof(T) == 4) {
         float4 *d4 = reinterpret_cast<float4 *>(dst);
-        d4[0] = make_float4(v[0], v[1], v[2], v[3]);
-        d4[1] = make_float4(v[4], v[5], v[6], v[7]);
+#pragma unroll
+        for (int q = 0; q < RUN / 4; ++q) d4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     } else {
         ulonglong2 *d2 = reinterpret_cast<ulonglong2 *>(dst);
 #pragma unroll
-        for (int q = 0; q < kRun / 2; ++q) {
+        for (int q = 0; q < RUN / 2; ++q) {
             ulonglong2 w;
             memcpy(&w.x, &v[2 * q], 8);
             memcpy(&w.y, &v[2 * q + 1], 8);
@@ -201,19 +202,19 @@ __device__ __forceinline__ void store_run(T *dst, const T (&v)[kRun]) {
 }
 
 // Values of the run from raw Sobol' words.
-template <int TR, typename T>
-__device__ __forceinline__ void run_from_u32(const uint32_t (&x)[kRun], T (&v)[kRun]) {
+template <int TR, typename T, int RUN = kRun>
+__device__ __forceinline__ void run_from_u32(const uint32_t (&x)[RUN], T (&v)[RUN]) {
     if constexpr (TR == RQMC_NORMAL && sizeof(T) == 4) {
-        Unif32 u[kRun];
-        float z[kRun];
+        Unif32 u[RUN];
+        float z[RUN];
 #pragma unroll
-        for (int k = 0; k < kRun; ++k) u[k] = unif32_from_u32(x[k]);
-        ndtri32_lockstep<kRun>(u, z);
+        for (int k = 0; k < RUN; ++k) u[k] = unif32_from_u32(x[k]);
+        ndtri32_lockstep<RUN>(u, z);
 #pragma unroll
-        for (int k = 0; k < kRun; ++k) v[k] = z[k];
+        for (int k = 0; k < RUN; ++k) v[k] = z[k];
     } else {
 #pragma unroll
-        for (int k = 0; k < kRun; ++k) v[k] = value_from_u32<TR, T>(x[k]);
+        for (int k = 0; k < RUN; ++k) v[k] = value_from_u32<TR, T>(x[k]);
     }
 }
 
@@ -365,12 +366,16 @@ __global__ void __launch_bounds__(256) points_run_kernel(const GenParams g, uint
     }
 }
 
-// Philox rows in runs: a warp task is (replication, block of 4 dimensions, kSegChunks chunks of
-// 256 points); a lane takes 8 consecutive points, one Philox call each gives the point's 4
-// coordinates of the block, and the lane writes each of the 4 rows' 8 values with vector stores.
+// Philox rows in runs: a warp task is (replication, block of 4 dimensions, 2048 consecutive
+// points); a lane takes runs of PR consecutive points, one Philox call each gives the point's 4
+// coordinates of the block, and the lane writes each of the 4 rows' PR values with vector stores.
 template <int TR, typename T>
 __global__ void __launch_bounds__(256) points_run_philox_kernel(const GenParams g, uint32_t N, uint32_t tasks_per_row,
                                                                 unsigned long long ntasks, T *__restrict__ out) {
+    // FP32 normals take runs of 4 points: the 4 x 4 Philox words and the inverse-CDF state
+    // fit in 71 registers (3 CTAs per SM) instead of 109
+    constexpr int PR = TR == RQMC_NORMAL && sizeof(T) == 4 ? 4 : kRun;
+    constexpr uint32_t chunk = 32u * PR;
     const uint32_t lane = threadIdx.x & 31;
     const unsigned long long warps = (unsigned long long)gridDim.x * (blockDim.x >> 5);
     const uint32_t seg_pts = 32u * kRun * kSegChunks;
@@ -380,13 +385,13 @@ __global__ void __launch_bounds__(256) points_run_philox_kernel(const GenParams 
         const unsigned long long rb = w / tasks_per_row;   // (m, block of 4 dimensions)
         const uint32_t seg0 = (uint32_t)(w % tasks_per_row) * seg_pts;
         const int m = (int)(rb / nb), jb = (int)(rb % nb);
-        for (int c = 0; c < kSegChunks; ++c) {
-            if (seg0 + 256u * c >= N) break;   // warp-uniform
-            const uint32_t i0 = seg0 + 256u * c + kRun * lane;
+        for (uint32_t c = 0; c < seg_pts / chunk; ++c) {
+            if (seg0 + chunk * c >= N) break;   // warp-uniform
+            const uint32_t i0 = seg0 + chunk * c + PR * lane;
             if (i0 >= N) continue;
-            uint32_t x[4][kRun];
+            uint32_t x[4][PR];
 #pragma unroll
-            for (int k = 0; k < kRun; ++k) {
+            for (int k = 0; k < PR; ++k) {
                 const unsigned long long n = g.offset + i0 + k;
                 const U32x4 r = philox4x32_10((uint32_t)n, (uint32_t)((n >> 32) & 0xFFFFu) | ((uint32_t)jb << 16),
                                               (uint32_t)m, kTagPath | (g.inst << 8), g.key0, g.key1);
@@ -399,9 +404,9 @@ __global__ void __launch_bounds__(256) points_run_philox_kernel(const GenParams 
             for (int q = 0; q < 4; ++q) {
                 const int j = 4 * jb + q;
                 if (j < g.s) {
-                    T v[kRun];
-                    run_from_u32<TR, T>(x[q], v);
-                    store_run<T>(out + ((size_t)m * g.s + j) * N + i0, v);
+                    T v[PR];
+                    run_from_u32<TR, T, PR>(x[q], v);
+                    store_run<T, PR>(out + ((size_t)m * g.s + j) * N + i0, v);
                 }
             }
         }

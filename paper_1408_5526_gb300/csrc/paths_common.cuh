@@ -150,26 +150,24 @@ __device__ __forceinline__ void sobol_lockstep(const uint32_t *__restrict__ Vj, 
 // tail branches only where some value needs them (about 0.3 % of the values).
 template <int P>
 __device__ __forceinline__ void ndtri32_lockstep(const Unif32 (&u)[P], float (&z)[P]) {
-    constexpr float C[] = RQMC_NDTRI_C;
-    float w[P], y[P], r[P];
+    float v[P], y[P], r[P];
     bool central = true;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
         const float q = u[p].q;
-        const float t = 4.0f * q * (1.0f - q);
-        w[p] = -0.6931471805599453f * lg2_approx(t);
+        v[p] = ndtri32_v(q);
         y[p] = fmaf(-2.0f, q, 1.0f);
-        central = central && w[p] < (float)RQMC_NDTRI_W_SPLIT;
-        r[p] = horner(C, w[p] - (float)RQMC_NDTRI_W_MID);
+        central = central && v[p] > (float)RQMC_NDTRI_V_SPLIT;
+        r[p] = erfinv_central32(v[p]);
     }
     if (!central) {
 #pragma unroll
         for (int p = 0; p < P; ++p)
-            if (w[p] >= (float)RQMC_NDTRI_W_SPLIT) r[p] = erfinv_ratio32(w[p]);
+            if (!(v[p] > (float)RQMC_NDTRI_V_SPLIT)) r[p] = erfinv_tail32(v[p]);
     }
 #pragma unroll
     for (int p = 0; p < P; ++p) {
-        const float x = 1.4142135623730951f * y[p] * r[p];
+        const float x = y[p] * r[p];
         z[p] = u[p].lower ? -x : x;
     }
 }

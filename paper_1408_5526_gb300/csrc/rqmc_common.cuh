@@ -357,7 +357,9 @@ struct PathGen {
 
 // ------------------------------------------------------------------ inverse normal CDF
 // erfinv(y)/y as a polynomial in w = -ln(4q(1-q)) (three branches, coefficients
-// fitted by fit_ndtri.py); Phi^-1(u) = -/+ sqrt(2) y P(w), y = 1 - 2q.
+// fitted by fit_ndtri.py); Phi^-1(u) = -/+ sqrt(2) y P(w), y = 1 - 2q.  The FP32 routines
+// take the central branch as one polynomial in v = log2(q(1-q)) = -w/ln 2 - 2 that includes
+// the factor sqrt(2) (RQMC_NDTRI_V), so no scaling or shift is spent before or after it.
 template <typename T, int N>
 __device__ __forceinline__ T horner(const T (&c)[N], T x) {
     T p = c[N - 1];
@@ -366,22 +368,28 @@ __device__ __forceinline__ T horner(const T (&c)[N], T x) {
     return p;
 }
 
-__device__ __forceinline__ float erfinv_ratio32(float w) {
-    constexpr float C[] = RQMC_NDTRI_C;
+// sqrt(2) erfinv(y)/y from v = log2(q(1-q)): central polynomial for v > V_SPLIT (w < W_SPLIT),
+// else the tail polynomials in sqrt(w).
+__device__ __forceinline__ float erfinv_central32(float v) {
+    constexpr float V[] = RQMC_NDTRI_V;
+    return horner(V, v);
+}
+__device__ __forceinline__ float erfinv_tail32(float v) {
     constexpr float T[] = RQMC_NDTRI_T;
     constexpr float U[] = RQMC_NDTRI_U;
-    if (w < (float)RQMC_NDTRI_W_SPLIT) return horner(C, w - (float)RQMC_NDTRI_W_MID);
+    const float w = -0.6931471805599453f * (v + 2.0f);
     const float sw = sqrt_approx(w);
-    if (w < (float)RQMC_NDTRI_W_SPLIT2) return horner(T, sw - (float)RQMC_NDTRI_T_MID);
-    return horner(U, sw - (float)RQMC_NDTRI_U_MID);
+    const float r = w < (float)RQMC_NDTRI_W_SPLIT2 ? horner(T, sw - (float)RQMC_NDTRI_T_MID)
+                                                   : horner(U, sw - (float)RQMC_NDTRI_U_MID);
+    return 1.4142135623730951f * r;
 }
+__device__ __forceinline__ float ndtri32_v(float q) { return lg2_approx(q * (1.0f - q)); }
 
 __device__ __forceinline__ float ndtri32(Unif32 v) {
     const float q = v.q;
-    const float t = 4.0f * q * (1.0f - q);
-    const float w = -0.6931471805599453f * lg2_approx(t);
+    const float lv = ndtri32_v(q);
     const float y = fmaf(-2.0f, q, 1.0f);
-    const float x = 1.4142135623730951f * y * erfinv_ratio32(w);
+    const float x = y * (lv > (float)RQMC_NDTRI_V_SPLIT ? erfinv_central32(lv) : erfinv_tail32(lv));
     return v.lower ? -x : x;
 }
 
