@@ -135,9 +135,10 @@ __global__ void __launch_bounds__(256) points_kernel(const GenParams g, uint32_t
 //   Halton/Rasrap: Algorithm 2's odometer restated for SIMD lanes.  Write the low part of the
 //   run's first point as q p + d0; the run's points are d = d0 + k (k < 8) with q, or, past a
 //   wrap of the lowest digit, d - p with q + 1.  With the permuted digit sums of the higher
-//   digits R'(q) and R'(q + 1) computed once per run, a point costs one digit increment and
-//   one sigma lookup: R = sigma(d) p^(L-1) + R'(.).  For p >= 7 a run wraps at most once;
-//   bases 2, 3 and 5 take the direct digit expansion.
+//   digits R'(q) and R'(q + 1) computed once per run, a point costs one sigma lookup:
+//   R = sigma(d) p^(L-1) + R'(.).  FP32 uniforms and normals never form R: the exact side
+//   test and the value follow from sigma(d) and per-run constants (HaltonRow::split).  For
+//   p >= 7 a run wraps at most once; bases 2, 3 and 5 take the direct digit expansion.
 constexpr int kRun = 8;
 constexpr int kSegChunks = 8;
 
@@ -225,9 +226,23 @@ struct HaltonRow {
     double invD;
     uint32_t pL, thr0, thr1;   // halton_lower(h, R, c) is R < thr_c
     float inv_pL, a0, a1, b0, b1;
+    // the split R = sigma(d) p^(L-1) + R' of the FP32 runs (run_halton32): thr_c = thi_c p^(L-1) + tlo_c
+    uint32_t pLm1, thi0, tlo0, thi1, tlo1;
+    float inv_p, pm1f;
     __device__ __forceinline__ explicit HaltonRow(const HaltonDim &h)
         : P(h.P), S0(h.S[0]), S1(h.S[1]), invD(h.invD), pL(h.pL), thr0((h.pL >> 1) + (h.tie & 1u)),
-          thr1((h.pL >> 1) + ((h.tie >> 1) & 1u)), inv_pL(h.inv_pL), a0(h.a[0]), a1(h.a[1]), b0(h.b[0]), b1(h.b[1]) {}
+          thr1((h.pL >> 1) + ((h.tie >> 1) & 1u)), inv_pL(h.inv_pL), a0(h.a[0]), a1(h.a[1]), b0(h.b[0]), b1(h.b[1]),
+          pLm1(h.pL / h.p), thi0(thr0 / pLm1), tlo0(thr0 % pLm1), thi1(thr1 / pLm1), tlo1(thr1 % pLm1),
+          inv_p(1.0f / (float)h.p), pm1f((float)(h.p - 1u)) {}
+    // Run constants of the points with higher-digit sum R' and carry c: the point with lowest
+    // digit sigma = sigma(d) has R = sigma p^(L-1) + R' and lies in the lower half exactly when
+    // sigma < T (R < thr_c, R' < p^(L-1)); then u = sigma / p + A, else 1 - u with
+    // 1 - u = (p - 1 - sigma) / p + B:  A = R' / p^L + a_c,  B = (p^(L-1) - 1 - R') / p^L + b_c.
+    __device__ __forceinline__ void split(uint32_t Rp, uint32_t c, uint32_t &T, float &A, float &B) const {
+        T = (c ? thi1 : thi0) + (Rp < (c ? tlo1 : tlo0) ? 1u : 0u);
+        A = fmaf((float)Rp, inv_pL, c ? a1 : a0);
+        B = fmaf((float)(pLm1 - 1u - Rp), inv_pL, c ? b1 : b0);
+    }
     __device__ __forceinline__ unsigned long long num(uint32_t R, uint32_t c) const {
         return (unsigned long long)R * P + (c ? S1 : S0);
     }
@@ -245,6 +260,79 @@ struct HaltonRow {
         return Unif64{((double)(lo ? n : D1 - n) + 0.5) * invD, lo};
     }
 };
+
+// One lane's run of kRun points (p >= 7): lowest digit d0 of its first point, the higher-digit
+// sums R'(q0) and R'(q0 + 1) and the carries before and after the wrap of the lowest digit
+// (R1 = R0 where no lane of the warp wraps).
+struct HaltonRun {
+    uint32_t d0, R0, R1, c0, c1;
+    bool any_wrap;   // warp-uniform: some lane's run wraps its lowest digit
+};
+__device__ __forceinline__ HaltonRun halton_run(const HaltonDim &h, const uint16_t *__restrict__ sg, uint32_t i0,
+                                                uint32_t pLm1) {
+    HaltonRun r;
+    uint32_t low = h.lo0 + i0;
+    r.c0 = low >= h.pL ? 1u : 0u;
+    low -= r.c0 ? h.pL : 0u;
+    uint32_t q0 = __umulhi(low, h.magic);
+    r.d0 = low - q0 * h.p;
+    if ((int32_t)r.d0 < 0) {
+        r.d0 += h.p;
+        q0 -= 1;
+    }
+    // the run reaches p^L: the low part wraps into the carry (and q0 + 1 to 0)
+    r.c1 = q0 + 1 == pLm1 ? 1u : r.c0;
+    // R'(q0 + 1) only where some lane's run wraps its lowest digit: always for small p, in
+    // about 256/p of the warps for p > 256
+    r.any_wrap = __any_sync(0xffffffffu, r.d0 + (kRun - 1) >= h.p);
+    if (r.any_wrap) {
+        halton_high2(h, sg, q0, &r.R0, &r.R1);
+    } else {
+        r.R0 = halton_high(h, sg, q0);
+        r.R1 = r.R0;
+    }
+    return r;
+}
+
+// FP32 uniforms or normals of a run (p >= 7) from the split of HaltonRow::split: a point costs
+// one permutation lookup (the padded table, see kSigPad), one integer compare and two FMAs.
+template <int TR>
+__device__ __forceinline__ void run_halton32(const HaltonRow &hr, const HaltonRun &r, const uint16_t *__restrict__ sg,
+                                             uint32_t p, float (&v)[kRun]) {
+    uint32_t T0;
+    float A0, B0;
+    hr.split(r.R0, r.c0, T0, A0, B0);
+    const uint16_t *sb = sg + r.d0;   // sb[k] = sigma((d0 + k) mod p)
+    Unif32 u[kRun];
+    if (!r.any_wrap) {
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) {
+            const uint32_t sk = sb[k];
+            const float fs = (float)sk;
+            const bool lo = sk < T0;
+            u[k] = Unif32{lo ? fmaf(fs, hr.inv_p, A0) : fmaf(hr.pm1f - fs, hr.inv_p, B0), lo};
+        }
+    } else {
+        uint32_t T1;
+        float A1, B1;
+        hr.split(r.R1, r.c1, T1, A1, B1);
+        const uint32_t kw = p - r.d0;   // points k >= kw are past the wrap: R'(q0 + 1), carry c1
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) {
+            const bool w = (uint32_t)k >= kw;
+            const uint32_t sk = sb[k];
+            const float fs = (float)sk;
+            const bool lo = sk < (w ? T1 : T0);
+            u[k] = Unif32{lo ? fmaf(fs, hr.inv_p, w ? A1 : A0) : fmaf(hr.pm1f - fs, hr.inv_p, w ? B1 : B0), lo};
+        }
+    }
+    if constexpr (TR == RQMC_NORMAL) {
+        ndtri32_lockstep<kRun>(u, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) v[k] = u[k].lower ? u[k].q : 1.0f - u[k].q;
+    }
+}
 
 template <int TR, typename T>
 __device__ __forceinline__ void run_from_halton(const HaltonRow &h, const uint32_t (&R)[kRun],
@@ -272,6 +360,31 @@ __device__ __forceinline__ void run_from_halton(const HaltonRow &h, const uint32
             v[k] = TR == RQMC_NORMAL ? ndtri64(w) : (w.lower ? w.q : 1.0 - w.q);
         }
     }
+}
+
+// Any transform and precision: the run's integer digit sums R (the odometer for p >= 7, the
+// digit expansion for bases 2, 3 and 5), then the values of unif32/unif64_halton.
+template <int TR, typename T>
+__device__ __forceinline__ void run_halton_digits(const HaltonRow &hr, const HaltonDim &h,
+                                                  const uint16_t *__restrict__ sg, uint32_t i0, uint32_t pLm1,
+                                                  T (&v)[kRun]) {
+    uint32_t R[kRun], cc[kRun];
+    if (h.p >= 7) {
+        const HaltonRun r = halton_run(h, sg, i0, pLm1);
+        const uint32_t kw = h.p - r.d0;
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) {
+            const bool w = (uint32_t)k >= kw;
+            R[k] = (uint32_t)sg[r.d0 + k] * pLm1 + (w ? r.R1 : r.R0);
+            cc[k] = w ? r.c1 : r.c0;
+        }
+    } else {
+        uint32_t ii[kRun];
+#pragma unroll
+        for (int k = 0; k < kRun; ++k) ii[k] = i0 + k;
+        halton_R_lockstep<kRun>(h, sg, ii, R, cc);
+    }
+    run_from_halton<TR, T>(hr, R, cc, v);
 }
 
 template <int TR, typename T, int SEQ>
@@ -322,44 +435,13 @@ __global__ void __launch_bounds__(256) points_run_kernel(const GenParams g, uint
             for (int c = 0; c < kSegChunks; ++c) {
                 if (seg0 + 256u * c >= N) break;   // warp-uniform
                 const uint32_t i0 = min(seg0 + 256u * c + kRun * lane, N - kRun);   // past the end: a valid run, not stored
-                uint32_t R[kRun], cc[kRun];
-                if (h.p >= 7) {
-                    uint32_t low = h.lo0 + i0;
-                    const uint32_t c0 = low >= h.pL ? 1u : 0u;
-                    low -= c0 ? h.pL : 0u;
-                    uint32_t q0 = __umulhi(low, h.magic);
-                    uint32_t d0 = low - q0 * h.p;
-                    if ((int32_t)d0 < 0) {
-                        d0 += h.p;
-                        q0 -= 1;
-                    }
-                    // the run reaches p^L: the low part wraps into the carry (and q0 + 1 to 0)
-                    const uint32_t c1 = q0 + 1 == pLm1 ? 1u : c0;
-                    // R'(q0 + 1) only where some lane's run wraps its lowest digit: always for
-                    // small p, in about 256/p of the warps for p > 256
-                    uint32_t R0, R1;
-                    if (__any_sync(0xffffffffu, d0 + (kRun - 1) >= h.p)) {
-                        halton_high2(h, sg, q0, &R0, &R1);
-                    } else {
-                        R0 = halton_high(h, sg, q0);
-                        R1 = R0;
-                    }
-#pragma unroll
-                    for (int k = 0; k < kRun; ++k) {
-                        uint32_t d = d0 + k;
-                        const bool wrap = d >= h.p;
-                        d -= wrap ? h.p : 0u;
-                        R[k] = (uint32_t)sg[d] * pLm1 + (wrap ? R1 : R0);
-                        cc[k] = wrap ? c1 : c0;
-                    }
-                } else {
-                    uint32_t ii[kRun];
-#pragma unroll
-                    for (int k = 0; k < kRun; ++k) ii[k] = i0 + k;
-                    halton_R_lockstep<kRun>(h, sg, ii, R, cc);
-                }
                 T v[kRun];
-                run_from_halton<TR, T>(hr, R, cc, v);
+                if constexpr (sizeof(T) == 4 && TR != RQMC_RAW) {
+                    if (h.p >= 7) run_halton32<TR>(hr, halton_run(h, sg, i0, pLm1), sg, h.p, v);
+                    else run_halton_digits<TR, T>(hr, h, sg, i0, pLm1, v);
+                } else {
+                    run_halton_digits<TR, T>(hr, h, sg, i0, pLm1, v);
+                }
                 if (seg0 + 256u * c + kRun * lane < N) store_run<T>(dst + i0, v);
             }
         }

@@ -85,6 +85,11 @@ enum Seq : int { kHaltonRS = 0, kRasrap = 1, kSobolDS = 2, kPhilox = 3, kSobolLM
 //   num  = R * P + S[c]                 (P = p^(K+1-L); S[c] = the permuted high digits
 //                                        of (n0+offset) div p^L + c at positions L..K)
 // num / p^(K+1) is exactly the point of eq. (perm) with all K start positions permuted.
+// Each dimension's permutation sigma(0..p-1) is followed by sigma(0..kSigPad-1) once more (indices
+// taken mod p), so that sigma of d = d0 + k, k < kSigPad, with d0 < p, is entry d0 + k whether
+// or not the lowest digit wraps.
+constexpr uint32_t kSigPad = 8;
+
 struct __align__(16) HaltonDim {
     unsigned long long P;
     unsigned long long S[2];
@@ -92,6 +97,7 @@ struct __align__(16) HaltonDim {
     uint32_t p, L, pL, lo0;
     uint32_t magic;          // floor(2^32 / p) + 1: q = umulhi(x, magic) is floor(x/p) or one more
     uint32_t sig_off;        // offset of sigma_{m,j} inside replication m's permutation table
+                             // (p entries, then sigma(0..kSigPad-1) again, see kSigPad)
     float inv_pL;            // FP32 conversion: u = R / p^L + (S[c] + 1/2) / D
     float a[2];              // (S[c] + 1/2) / D
     float b[2];              // (P - 1 - S[c] + 1/2) / D, the complement's tail

@@ -135,6 +135,7 @@ __global__ void setup_halton_kernel(const BaseConst *__restrict__ bases, int s, 
             sg[r] = tmp;
         }
     }
+    for (uint32_t a = 0; a < kSigPad; ++a) sg[b.p + a] = sg[a % b.p];
     // split of n0 + offset at digit L
     const unsigned long long n0o = n0 + offset;
     bool ok = n0o >= n0 && n0o <= b.D - N;   // n0 + offset + N - 1 < p^(K+1)
@@ -248,7 +249,7 @@ rqmc_status generator_layout(Plan &pl, Carve &cv, GenLayout &gl) {
             b.sig_off = (uint32_t)off;
             b.inv_pL = (float)(1.0 / (double)b.pL);
             b.invD = 1.0 / (double)b.D;
-            off += b.p;
+            off += b.p + kSigPad;
         }
         gl.sig_len = off;
         gl.hdim_off = cv.take(sizeof(HaltonDim) * (size_t)M * s);
