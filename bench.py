@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 512 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one lmm_caplet_kernel<40, 1, float> launch
 # (Rasrap) of this workload, from an ncu capture of the kernel as committed; None whenever
 # that kernel has changed since the capture.
-LMM_TRAFFIC_BYTES = 711.7e3
+LMM_TRAFFIC_BYTES = None
 
 
 def _peaks():
@@ -59,7 +59,7 @@ def _peaks():
 
 
 def lmm_algorithmic_ops(nf, nK, paths):
-    """Source-level operations of one fused caplet launch.
+    """Source-level operations of one caplet plan execute (normals, paths, payoffs).
     MUFU: ex2 + rcp per forward update; per step lg2 (inverse CDF) and ex2 + rcp
     (fixed forward and numeraire).  Returned as SFU issue slots: on GB300 ex2 issues at
     32 per SM per clock and rcp/lg2 at 16, so an ex2 counts half a slot.
@@ -285,7 +285,8 @@ def run_ours(args, rank, world):
     pk = Peaks(sms, probe)
     mufu, fma = lmm_algorithmic_ops(N_FWD, nK, N_PATHS * M_REPL)
     per_launch_s = statistics.mean(launch_ms) / 1e3
-    roof = pk.alu(mufu, fma, per_launch_s, "lmm_caplet_kernel<40,SEQ,float> + theta_kernel")
+    roof = pk.alu(mufu, fma, per_launch_s, "one plan execute: points_run_kernel normals + "
+                  "lmm_caplet_kernel<40,float> (normals loaded) + theta_kernel")
     roof.update({"traffic": LMM_TRAFFIC_BYTES,
                  "traffic_unit": "DRAM bytes per launch (ncu, Rasrap launch; tables only)" if LMM_TRAFFIC_BYTES
                  else "not captured since the kernel last changed",

@@ -69,6 +69,10 @@ void set_reduction(Plan &pl, int nout, int threads, int ppt) {
     r.N = (uint32_t)pl.N;
 }
 
+// Largest normals buffer of an FP32 caplet plan; above it the caplet kernel generates its
+// normals itself.
+static constexpr size_t kMaxNormalsBytes = 8ull << 30;
+
 // Allocates one device block: generator tables, model tables, status words, partials
 // (sized for the smallest tile, 32 paths, so launch knobs can change later).
 static rqmc_status finish_plan(Plan *pl, const std::vector<unsigned char> &model, size_t model_align,
@@ -119,6 +123,7 @@ static void destroy(Plan *pl, cudaStream_t st) {
     if (!pl) return;
     if (pl->kind == kBatch) batch_destroy(*pl);
     if (pl->d_buf) cudaFreeAsync(pl->d_buf, st);
+    if (pl->znorm) cudaFreeAsync(pl->znorm, st);
     if (pl->adj_buf) {
         cudaStreamSynchronize(st);
         cudaFree(pl->adj_buf);
@@ -317,6 +322,19 @@ extern "C" rqmc_status rqmc_plan_caplets(const rqmc_lmm_params *p, const double 
     rs = finish_plan(pl, {}, 16, partial_capacity(*pl, nout), 0, nullptr);
     if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
     pl->launches = 2;
+    // FP32: the normals come from the point-stream run kernel, which shares the digit and bit
+    // work of consecutive points, and the caplet kernel reads one per path and step
+    const size_t zbytes = sizeof(float) * (size_t)M * (size_t)pl->s * (size_t)N;
+    if (prec == RQMC_FP32 && points_runs_eligible(*pl) && zbytes <= kMaxNormalsBytes) {
+        cudaError_t e = cudaMallocAsync(&pl->znorm, zbytes, 0);
+        if (e != cudaSuccess) {
+            pl->znorm = nullptr;
+            destroy(pl, 0);
+            set_error(std::string("device allocation failed (normals): ") + cudaGetErrorString(e));
+            return RQMC_ENOMEM;
+        }
+        pl->launches = 3;
+    }
     *plan = pl;
     return RQMC_OK;
 }
@@ -409,7 +427,10 @@ extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, voi
     }
     switch (plan->kind) {
         case kProduct: e = launch_product(*plan, st); break;
-        case kCaplets: e = launch_caplets(*plan, st); break;
+        case kCaplets:
+            e = plan->znorm ? launch_points(*plan, RQMC_NORMAL, plan->znorm, st) : cudaSuccess;
+            if (e == cudaSuccess) e = launch_caplets(*plan, st);
+            break;
         case kMbs: e = launch_mbs(*plan, st); break;
         case kAdjoint: e = launch_adjoint(*plan, st); break;
         default: set_error("plan kind cannot be executed"); return RQMC_EUNSUPPORTED;

@@ -150,19 +150,20 @@ __device__ __forceinline__ void lmm_fill_constants(const LmmModel<T> &md, typena
     for (int k = threadIdx.x; k < NF; k += blockDim.x) X0[k] = md.X0[k];
 }
 
-// Shared memory: [generator stage][constants][X0 x NF, K x 8][normals 8 x threads]
+// Shared memory: [generator stage][constants][X0 x NF, K x 8][normals zsets x 8 x P x threads]
 //                [transpose buffers][acc][cmp]
+// zsets = 2 when the normals are loaded: the next block's are copied in while a block runs.
 template <int NF, typename T, int P = 1>
 __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, int nw, int nK, int nout,
                                                            size_t *o_cst, size_t *o_x0, size_t *o_z, size_t *o_buf,
-                                                           size_t *o_acc) {
+                                                           size_t *o_acc, int zsets = 1) {
     size_t off = stage_bytes(g);
     *o_cst = off;
     off = align16(off + sizeof(typename LmmMath<T>::C) * lmm_cst_count<NF, T>());
     *o_x0 = off;
     off = align16(off + sizeof(T) * (NF + kMaxStrikes));
     *o_z = off;
-    off = align16(off + sizeof(T) * 8 * P * 32 * (size_t)nw);
+    off = align16(off + sizeof(T) * 8 * P * 32 * (size_t)nw * (size_t)zsets);
     *o_buf = off;
     off = align16(off + sizeof(T) * (size_t)nw * 8 * nK * LmmMath<T>::PAD);
     *o_acc = off;
@@ -186,10 +187,14 @@ constexpr int lmm_min_blocks() {
 // the P paths) into the warp's transpose buffer, block sums into the warp's Kahan
 // accumulators (wacc/wcmp, indexed by output t nK + k).  The P paths share every constant
 // load and all control flow, and give each warp P independent dependency chains.
-template <int NF, int SEQ, typename T, int P, bool EU = false>
+// ZG: the normals are not generated here but read from zg, the replication's normals
+// [step][N] written beforehand by the point-stream kernel from the plan's own generator:
+// path i takes zg[t N + i], copied into the thread's shared columns a block ahead.
+template <int NF, int SEQ, typename T, int P, bool EU = false, bool ZG = false>
 __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&active)[P], const LmmScal<T> &sc,
                                          const typename LmmMath<T>::C *cst, const T *X0, const T *Ks, T *zb,
-                                         T *wbuf, T *wacc, T *wcmp, const int lane) {
+                                         T *wbuf, T *wacc, T *wcmp, const int lane, const T *zg = nullptr,
+                                         size_t zN = 0) {
     using M = LmmMath<T>;
     using CC = typename M::C;
     constexpr int PAD = M::PAD;
@@ -208,27 +213,49 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
 #pragma unroll
     for (int p = 0; p < P; ++p) disc[p] = sc.disc0;
     const int nblk = (nf + 7) >> 3;
+    // loaded normals: block bb's go to set bb & 1 of the thread's columns by asynchronous copies
+    auto zload = [&](const int bb) {
+        if (bb < nblk) {
+            const int nb = min(8, nf - 8 * bb);
+            T *dst = zb + (bb & 1) * 8 * zs;
+#pragma unroll
+            for (int tp = 0; tp < 8; ++tp)
+#pragma unroll
+                for (int p = 0; p < P; ++p)
+                    if (tp < nb) cp_async4(dst + tp * zs + p * blockDim.x, zg + (size_t)(8 * bb + tp) * zN + pg[p].i);
+        }
+        cp_async_commit();   // an empty group past the last block keeps the wait count uniform
+    };
+    if constexpr (ZG) zload(0);
     for (int b = 0; b < nblk; ++b) {
         const int ngrp = (nf - 8 * b + 7) >> 3;   // groups of 8 shifted slots still alive
         const CC *cb0 = cst + 8 * b;              // constants of original slot 8b + k (row 0)
         const int nst = min(8, nf - 8 * b);
-        // phase A: the block's normals (one short generator loop)
-        for (int tp = 0; tp < nst; ++tp) {
-            if constexpr (sizeof(T) == 4) {
-                float z[P];
-                normals32<SEQ, P>(pg, 8 * b + tp, z);
+        // phase A: the block's normals (copied in during the previous block, or one short
+        // generator loop)
+        T *zbb = zb;
+        if constexpr (ZG) {
+            zload(b + 1);          // the set it overwrites was last read in block b - 1
+            cp_async_wait<1>();    // block b's copies have landed
+            zbb = zb + (b & 1) * 8 * zs;
+        } else {
+            for (int tp = 0; tp < nst; ++tp) {
+                if constexpr (sizeof(T) == 4) {
+                    float z[P];
+                    normals32<SEQ, P>(pg, 8 * b + tp, z);
 #pragma unroll
-                for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = z[p];
-            } else {
+                    for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = z[p];
+                } else {
 #pragma unroll
-                for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = Draw<T>::normal(pg[p], 8 * b + tp);
+                    for (int p = 0; p < P; ++p) zb[tp * zs + p * blockDim.x] = Draw<T>::normal(pg[p], 8 * b + tp);
+                }
             }
         }
         // phase B: forward updates and payoffs (each thread reads back its own columns)
         for (int tp = 0; tp < nst; ++tp) {
             T W[P];
 #pragma unroll
-            for (int p = 0; p < P; ++p) W[p] = sqhc * zb[tp * zs + p * blockDim.x];
+            for (int p = 0; p < P; ++p) W[p] = sqhc * zbb[tp * zs + p * blockDim.x];
             const CC *cb = GT ? cb0 + (size_t)(8 * b + tp) * NF : cb0;   // this step's row
             // slot k of the P paths: FP32 pairs share a reciprocal, an odd path goes alone
             auto update_slot = [&](const int k, const CC c) {
@@ -314,8 +341,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
                 T pay = T(0);
 #pragma unroll
                 for (int p = 0; p < P; ++p) {
-                    const T x = Lf[p] - K;
-                    pay += x > T(0) ? x * dd[p] : T(0);
+                    pay = fmaT(fmax(Lf[p] - K, T(0)), dd[p], pay);
                 }
                 row[kk * PAD] = pay;
             }
@@ -350,8 +376,11 @@ constexpr int lmm_ilp() {
 #endif
 }
 
-template <int NF, int SEQ, typename T, bool EU>
-__global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kernel(const GenParams g, const LmmModel<T> md, const RedParams r) {
+// ZG: normals read from zg ([M][nf][N], see lmm_path); g.stage is then 0 and no generator
+// table is staged.
+template <int NF, int SEQ, typename T, bool EU, bool ZG>
+__global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kernel(const GenParams g, const LmmModel<T> md, const RedParams r,
+                                                                            const T *__restrict__ zg) {
     using M = LmmMath<T>;
     using CC = typename M::C;
     constexpr int PAD = M::PAD;
@@ -360,8 +389,8 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     const int nK = md.nK, nout = r.nout;
     constexpr int P = lmm_ilp<NF, T>();
     size_t o_cst, o_x0, o_z, o_buf, o_acc;
-    lmm_smem_layout<NF, T, P>(g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc);
-    T *zb = reinterpret_cast<T *>(smem_raw + o_z) + threadIdx.x;   // [8][P][blockDim], own columns
+    lmm_smem_layout<NF, T, P>(g, nw, nK, nout, &o_cst, &o_x0, &o_z, &o_buf, &o_acc, ZG ? 2 : 1);
+    T *zb = reinterpret_cast<T *>(smem_raw + o_z) + threadIdx.x;   // [zsets][8][P][blockDim], own columns
     CC *cst = reinterpret_cast<CC *>(smem_raw + o_cst);
     T *X0 = reinterpret_cast<T *>(smem_raw + o_x0);
     T *Ks = X0 + NF;
@@ -382,7 +411,8 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
         const uint32_t tile = u % r.tiles_per_m;
         if (m != staged_m) {
             __syncthreads();
-            stage_tables(g, m, smem_raw, gv);
+            if constexpr (ZG) view_tables(g, m, gv);
+            else stage_tables(g, m, smem_raw, gv);
             staged_m = m;
         }
         __syncthreads();
@@ -398,19 +428,22 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
                 pg[p].init(gv, active[p] ? i : 0u);
             }
             if (!__any_sync(0xffffffffu, any)) break;
-            lmm_path<NF, SEQ, T, P, EU>(pg, active, sc, cst, X0, Ks, zb, wbuf, wacc, wcmp, lane);
+            lmm_path<NF, SEQ, T, P, EU, ZG>(pg, active, sc, cst, X0, Ks, zb, wbuf, wacc, wcmp, lane,
+                                            ZG ? zg + (size_t)m * md.nf * r.N : nullptr, r.N);
         }
         flush_unit(r, u, acc, cmp);
     }
 }
 
-template <int NF, int SEQ, typename T>
+template <int NF, int SEQ, typename T, bool ZG = false>
 static cudaError_t launch_lmm_t(const Plan &pl, const LmmModel<T> &md, cudaStream_t st) {
-    auto kern = pl.scheme == RQMC_EULER ? lmm_caplet_kernel<NF, SEQ, T, true> : lmm_caplet_kernel<NF, SEQ, T, false>;
+    auto kern = pl.scheme == RQMC_EULER ? lmm_caplet_kernel<NF, SEQ, T, true, ZG> : lmm_caplet_kernel<NF, SEQ, T, false, ZG>;
+    GenParams g = pl.gen;
+    if (ZG) g.stage = 0;   // no generator table is read
     const int threads = pl.threads;
     size_t a, b, c, d, e2;
-    const size_t smem =
-        lmm_smem_layout<NF, T, lmm_ilp<NF, T>()>(pl.gen, threads / 32, md.nK, pl.red.nout, &a, &b, &c, &d, &e2);
+    const size_t smem = lmm_smem_layout<NF, T, lmm_ilp<NF, T>()>(g, threads / 32, md.nK, pl.red.nout, &a, &b, &c, &d,
+                                                                 &e2, ZG ? 2 : 1);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -422,7 +455,7 @@ static cudaError_t launch_lmm_t(const Plan &pl, const LmmModel<T> &md, cudaStrea
     if (occ < 1) occ = 1;
     unsigned grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)occ * sms);
     if (pl.grid > 0) grid = (unsigned)std::min<unsigned long long>(pl.red.units, (unsigned long long)pl.grid);
-    kern<<<grid, threads, smem, st>>>(pl.gen, md, pl.red);
+    kern<<<grid, threads, smem, st>>>(g, md, pl.red, ZG ? reinterpret_cast<const T *>(pl.znorm) : nullptr);
     return cudaGetLastError();
 }
 

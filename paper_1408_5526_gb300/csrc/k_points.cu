@@ -520,8 +520,11 @@ static cudaError_t launch_points_run(const Plan &pl, void *out, cudaStream_t st)
 // The run kernels apply when every run of 8 points starts on a 16-byte boundary (N a multiple
 // of 8, the buffer 16-byte aligned) and, for Sobol', the offset is a multiple of 8 (the runs'
 // index bits 0..2 are then the point's position in the run).
+bool points_runs_eligible(const Plan &pl) {
+    return pl.N % kRun == 0 && (pl.seq == kPhilox || pl.offset % kRun == 0);
+}
 static bool points_runs_apply(const Plan &pl, const void *out) {
-    return pl.N % kRun == 0 && (pl.seq == kPhilox || pl.offset % kRun == 0) && ((uintptr_t)out & 15u) == 0;
+    return points_runs_eligible(pl) && ((uintptr_t)out & 15u) == 0;
 }
 
 template <int TR, typename T>

@@ -61,6 +61,17 @@ __device__ __forceinline__ void warp_accumulate<double>(double v, double *acc, d
     if (lane == 0) acc[o] += v;
 }
 
+// Asynchronous 4-byte global -> shared copies (waited for by the issuing thread only).
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 

@@ -154,6 +154,9 @@ struct Plan {
     // device memory (one allocation)
     void *d_buf = nullptr;
     size_t d_bytes = 0;
+    // FP32 caplet plans: the paths' normals [M][n_fwd][N], written by the point-stream run
+    // kernel before the caplet kernel reads them (null: the caplet kernel generates them)
+    void *znorm = nullptr;
     // models
     LmmModel<float> lmm32{};
     LmmModel<double> lmm64{};
@@ -195,6 +198,8 @@ const std::vector<uint32_t> &sobol_directions();
 
 // ---- launchers (k_*.cu); all asynchronous on `st`
 cudaError_t launch_points(const Plan &pl, int tr, void *out, cudaStream_t st);
+// the point stream of pl takes the run kernels (N a multiple of 8, and so is the offset except for Philox)
+bool points_runs_eligible(const Plan &pl);
 cudaError_t launch_product(const Plan &pl, cudaStream_t st);
 cudaError_t launch_caplets(const Plan &pl, cudaStream_t st);
 cudaError_t launch_mbs(const Plan &pl, cudaStream_t st);
