@@ -17,7 +17,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "librqmc.so")
 SOURCES = ["api.cu", "setup.cu", "probe.cu", "k_points.cu", "k_product.cu", "k_lmm.cu", "k_lmm_halton.cu", "k_lmm_sobol.cu",
            "k_lmm_philox.cu", "k_lmm_loaded.cu", "k_mbs.cu", "noalloc.cu", "k_adjoint.cu", "k_adjoint_halton.cu",
-           "k_adjoint_sobol.cu", "k_adjoint_philox.cu", "batch.cu", "k_batch.cu", "k_batch_halton.cu",
+           "k_adjoint_sobol.cu", "k_adjoint_philox.cu", "k_adjoint_loaded.cu", "batch.cu", "k_batch.cu", "k_batch_halton.cu",
            "k_batch_sobol.cu", "k_batch_philox.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -432,7 +432,10 @@ extern "C" rqmc_status rqmc_plan_execute(rqmc_plan *plan, double *theta_dev, voi
             if (e == cudaSuccess) e = launch_caplets(*plan, st);
             break;
         case kMbs: e = launch_mbs(*plan, st); break;
-        case kAdjoint: e = launch_adjoint(*plan, st); break;
+        case kAdjoint:
+            e = plan->znorm ? launch_points(*plan, RQMC_NORMAL, plan->znorm, st) : cudaSuccess;
+            if (e == cudaSuccess) e = launch_adjoint(*plan, st);
+            break;
         default: set_error("plan kind cannot be executed"); return RQMC_EUNSUPPORTED;
     }
     if (e != cudaSuccess) return cuda_fail(e, "path kernel launch");
@@ -629,6 +632,21 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
     md->reverse = any_w ? 1 : 0;
     rs = finish_plan(pl, {}, 16, (size_t)pl->red.units * nout, 0, nullptr);
     if (rs != RQMC_OK) { destroy(pl, 0); return rs; }
+    // the normals from the point-stream run kernel, as for caplet plans (before the grid query:
+    // the kernels that read them are the ones launched).  Not for Philox: one counter call
+    // gives a path four coordinates, so generating them in the sweeps is cheaper than the
+    // buffer's round trip through HBM (66.6 against 68.8 ms at 80 forwards, two factors,
+    // N = 2^18, M = 32).
+    const size_t zbytes = sizeof(float) * (size_t)M * (size_t)pl->s * (size_t)N;
+    if (pl->seq != kPhilox && points_runs_eligible(*pl) && zbytes <= kMaxNormalsBytes) {
+        cudaError_t ez = cudaMallocAsync(&pl->znorm, zbytes, 0);
+        if (ez != cudaSuccess) {
+            pl->znorm = nullptr;
+            destroy(pl, 0);
+            set_error(std::string("device allocation failed (normals): ") + cudaGetErrorString(ez));
+            return RQMC_ENOMEM;
+        }
+    }
     pl->grid = adjoint_grid(*pl);
     if (pl->grid < 1) { destroy(pl, 0); set_error("adjoint: occupancy query failed"); return RQMC_ECUDA; }
     // per-thread columns (stride T): records, one float2 per step (the step's prefix total A);
@@ -649,7 +667,7 @@ extern "C" rqmc_status rqmc_plan_adjoint(const rqmc_lmm_params *p, const double 
         destroy(pl, 0);
         return cuda_fail(e, "adjoint scratch clear");
     }
-    pl->launches = 2;
+    pl->launches = pl->znorm ? 3 : 2;
     *plan = pl;
     return RQMC_OK;
 }

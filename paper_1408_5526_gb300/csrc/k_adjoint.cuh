@@ -70,9 +70,13 @@ __host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, s
 #define RQMC_ADJ_MIN_BLOCKS 2
 #endif
 
-template <int NF, int D, int SEQ>
+// ZG: the normals are read from zg ([M][D nf][N], written beforehand by the point-stream run
+// kernel from the plan's generator, one step ahead of their use) instead of generated; g.stage
+// is then 0 and no generator table is staged.
+template <int NF, int D, int SEQ, bool ZG = false>
 __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
-    lmm_adjoint_kernel(const GenParams g, const AdjModel md, const AdjScratch sc, const RedParams r) {
+    lmm_adjoint_kernel(const GenParams g, const AdjModel md, const AdjScratch sc, const RedParams r,
+                       const float *__restrict__ zg) {
     constexpr int BD = kAdjThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     size_t o_fw, o_rv, o_st;
@@ -105,7 +109,8 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
         const uint32_t tile = u % r.tiles_per_m;
         if (m != staged_m) {
             __syncthreads();
-            stage_tables(g, m, smem_raw, gv);
+            if constexpr (ZG) view_tables(g, m, gv);
+            else stage_tables(g, m, smem_raw, gv);
             staged_m = m;
         }
         __syncthreads();
@@ -115,6 +120,14 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
             if (!__any_sync(0xffffffffu, active)) break;
             PathGen<SEQ> pg;
             pg.init(gv, active ? i : 0u);
+            // loaded normals of step t: dims D t, D t + 1 of this path's column
+            const float *zrow = ZG ? zg + (size_t)m * (size_t)(D * nf) * r.N + pg.i : nullptr;
+            auto zload = [&](int t, float &a, float &b) {
+                a = zrow[(size_t)(D * t) * r.N];
+                b = D == 2 ? zrow[(size_t)(D * t + 1) * r.N] : 0.0f;
+            };
+            float zn0 = 0.0f, zn1 = 0.0f;
+            if constexpr (ZG) zload(0, zn0, zn1);
             // slots nf .. 4 nch - 1 are padding with zero volatility: they stay constant and feed
             // nothing into the drifts, the adjoints or the vegas, so full chunks need no checks
             for (int n = 0; n < 4 * nch; ++n) xcol[n * BD] = md.X0[n];
@@ -122,7 +135,11 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
             float disc = md.disc0, value = 0.0f;
             for (int t = 0; t < nf; ++t) {
                 float Az0, Az1 = 0.0f, A0 = 0.0f, A1 = 0.0f;
-                if constexpr (D == 2) {
+                if constexpr (ZG) {
+                    Az0 = sqhl * zn0;
+                    Az1 = sqhl * zn1;
+                    if (t + 1 < nf) zload(t + 1, zn0, zn1);
+                } else if constexpr (D == 2) {
                     float z0, z1;
                     normals32_two_dims<SEQ>(pg, 2 * t, 2 * t + 1, z0, z1);
                     Az0 = sqhl * z0;
@@ -181,6 +198,9 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
             // carry over in registers; the others are loaded two chunks ahead from the columns
             float4 top0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), top1 = top0;
             float2 At_next = md.reverse ? rec[(size_t)(nf - 1) * T] : make_float2(0.0f, 0.0f);
+            if constexpr (ZG) {
+                if (md.reverse) zload(nf - 1, zn0, zn1);
+            }
             for (int t = md.reverse ? nf - 1 : -1; t >= 0; --t) {
                 const int c0 = t >> 2, jt = t & 3;
                 const float2 At = At_next;
@@ -189,8 +209,15 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
                 float4 p0 = top0;
                 float4 p1 = nch - 2 >= c0 ? top1 : top0;
                 float Z0, Z1 = 0.0f;
-                if constexpr (D == 2) normals32_two_dims<SEQ>(pg, 2 * t, 2 * t + 1, Z0, Z1);
-                else Z0 = Draw<float>::normal(pg, t);
+                if constexpr (ZG) {
+                    Z0 = zn0;
+                    Z1 = zn1;
+                    if (t > 0) zload(t - 1, zn0, zn1);
+                } else if constexpr (D == 2) {
+                    normals32_two_dims<SEQ>(pg, 2 * t, 2 * t + 1, Z0, Z1);
+                } else {
+                    Z0 = Draw<float>::normal(pg, t);
+                }
                 // the fixed forward's post-step value is the column's current value
                 const float Y = xcol[t * BD];
                 const float e = ex2_approx(Y);
@@ -319,24 +346,29 @@ __global__ void __launch_bounds__(kAdjThreads, RQMC_ADJ_MIN_BLOCKS)
 
 namespace rqmc {
 
-template <int NF, int D, int SEQ>
+template <int NF, int D, int SEQ, bool ZG = false>
 static cudaError_t launch_adj_t(const Plan &pl, cudaStream_t st) {
-    auto kern = lmm_adjoint_kernel<NF, D, SEQ>;
+    auto kern = lmm_adjoint_kernel<NF, D, SEQ, ZG>;
+    GenParams g = pl.gen;
+    if (ZG) g.stage = 0;   // no generator table is read
     size_t a, b, c;
-    const size_t smem = adj_smem_layout<NF>(pl.gen, &a, &b, &c);
+    const size_t smem = adj_smem_layout<NF>(g, &a, &b, &c);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    kern<<<pl.grid, kAdjThreads, smem, st>>>(pl.gen, *pl.adjm, pl.adjs, pl.red);
+    kern<<<pl.grid, kAdjThreads, smem, st>>>(g, *pl.adjm, pl.adjs, pl.red,
+                                             ZG ? static_cast<const float *>(pl.znorm) : nullptr);
     return cudaGetLastError();
 }
 
-template <int NF, int D, int SEQ>
+template <int NF, int D, int SEQ, bool ZG = false>
 static int grid_adj_t(const Plan &pl, int mode) {
-    auto kern = lmm_adjoint_kernel<NF, D, SEQ>;
+    auto kern = lmm_adjoint_kernel<NF, D, SEQ, ZG>;
+    GenParams g = pl.gen;
+    if (ZG) g.stage = 0;
     size_t a, b, c;
-    const size_t smem = adj_smem_layout<NF>(pl.gen, &a, &b, &c);
+    const size_t smem = adj_smem_layout<NF>(g, &a, &b, &c);
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -347,15 +379,17 @@ static int grid_adj_t(const Plan &pl, int mode) {
 }
 
 // mode 0: launch, mode 1: return the persistent grid size
-template <int SEQ>
+// ZG: the kernels that read pl.znorm (one set for every sequence, instantiated only by
+// k_adjoint_loaded.cu)
+template <int SEQ, bool ZG = false>
 int adjoint_seq(const Plan &pl, cudaStream_t st, int mode) {
     const bool two = pl.adjm->d == 2;
     if (pl.nf_bucket == 40) {
-        if (mode) return two ? grid_adj_t<40, 2, SEQ>(pl, mode) : grid_adj_t<40, 1, SEQ>(pl, mode);
-        return (int)(two ? launch_adj_t<40, 2, SEQ>(pl, st) : launch_adj_t<40, 1, SEQ>(pl, st));
+        if (mode) return two ? grid_adj_t<40, 2, SEQ, ZG>(pl, mode) : grid_adj_t<40, 1, SEQ, ZG>(pl, mode);
+        return (int)(two ? launch_adj_t<40, 2, SEQ, ZG>(pl, st) : launch_adj_t<40, 1, SEQ, ZG>(pl, st));
     }
-    if (mode) return two ? grid_adj_t<80, 2, SEQ>(pl, mode) : grid_adj_t<80, 1, SEQ>(pl, mode);
-    return (int)(two ? launch_adj_t<80, 2, SEQ>(pl, st) : launch_adj_t<80, 1, SEQ>(pl, st));
+    if (mode) return two ? grid_adj_t<80, 2, SEQ, ZG>(pl, mode) : grid_adj_t<80, 1, SEQ, ZG>(pl, mode);
+    return (int)(two ? launch_adj_t<80, 2, SEQ, ZG>(pl, st) : launch_adj_t<80, 1, SEQ, ZG>(pl, st));
 }
 
 }  // namespace rqmc

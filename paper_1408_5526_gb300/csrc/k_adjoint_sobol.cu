@@ -2,5 +2,5 @@
 #include "k_adjoint.cuh"
 
 namespace rqmc {
-template int adjoint_seq<kSobolDS>(const Plan &pl, cudaStream_t st, int mode);
+template int adjoint_seq<kSobolDS, false>(const Plan &pl, cudaStream_t st, int mode);
 }  // namespace rqmc
