@@ -15,10 +15,12 @@
 // costs ex2 + rcp + 4 FP32 ops: a = 1 / (1 + 2^-X), W += (h sigma_n) a, X += sigma_n W + cc_n.
 // FP32 strips of up to 40 forwards drop the + cc_n: they carry X~_n = X_n - t cc_n and read,
 // per step t and forward n, the constant g = 2^(-t cc_n) from a table, so that 1 + 2^-X =
-// 1 + g 2^-X~ is one FMA.  Two lockstep paths share one reciprocal, 1/d0 = d1 / (d0 d1) and
-// 1/d1 = d0 / (d0 d1), multiplied once by h sigma_n: per forward and pair of paths two ex2,
-// one rcp and eight FP32 operations.  Single-path strips (80 and 160 forwards) pair adjacent
-// forwards the same way outside the first group of a block.  Forward n sits in slot n-1 of an
+// 1 + g 2^-X~ is one FMA.  In FP32 the factor h sigma_n is folded into the denominator,
+// d' = (1 + g 2^-X~) / (h sigma_n) = G 2^-X~ + H with the constants G = g / (h sigma_n) and
+// H = 1 / (h sigma_n), so that the drift term h sigma_n a_n is 1/d'.  Two lockstep paths share
+// one reciprocal, 1/d0' = d1' / (d0' d1') and 1/d1' = d0' / (d0' d1'): per forward and pair of
+// paths two ex2, one rcp and seven FP32 operations.  Single-path strips (80 and 160 forwards)
+// pair adjacent forwards the same way outside the first group of a block.  Forward n sits in slot n-1 of an
 // NF-slot array (NF = 16/40/80/160).  Steps run in blocks of 8; after each block the
 // array shifts down by 8 slots, so at step tp of a block the alive slots are tp..7 of
 // group 0 (entered through an 8-way fall-through switch) plus whole groups of 8 that a
@@ -52,6 +54,12 @@ struct LmmMath<float> {
                      : "r"((unsigned)__cvta_generic_to_shared(p)));
         return v;
     }
+    static __device__ __forceinline__ float2 lds2(const float2 *p) {
+        float2 v;
+        asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y)
+                     : "r"((unsigned)__cvta_generic_to_shared(p)));
+        return v;
+    }
 };
 template <>
 struct LmmMath<double> {
@@ -74,15 +82,36 @@ template <int NF, typename T>
 __host__ __device__ constexpr bool lmm_gtab() {
     return sizeof(T) == 4 && NF <= 40;
 }
+// FP32 strips of 80 and 160 forwards (one path per thread) use the pair table: per pair q of
+// adjacent slots (2q, 2q + 1) the static (sigma, H, sigma, H) as one float4, per step t and pair
+// the (G, G) of the two slots as one float2, and per step the fixing factor 2^((t+1) cc_t).
+template <int NF, typename T>
+__host__ __device__ constexpr bool lmm_ptab() {
+    return sizeof(T) == 4 && NF > 40;
+}
 
-// One forward of one path.  Without the g-table c = (sigma, h sigma, cc, 0) and X is the
-// log-forward; with it c = (sigma, h sigma, 2^(-t cc), 2^(t cc)) and X = X~.
+// The folded drift constant H = 1 / (h sigma_n); a zero (or vanishing) h sigma_n is replaced by
+// 2^-40 of the same sign, whose drift term h sigma_n a_n <= 2^-40 is far below the FP32
+// rounding of W, so that d' and the product of a pair of them stay finite.
+__host__ __device__ __forceinline__ float lmm_fold_inv(float hs) {
+    const float m = 9.094947e-13f;   // 2^-40
+    return 1.0f / (fabsf(hs) < m ? copysignf(m, hs) : hs);
+}
+
+// One forward of one path.  FP64: c = (sigma, h sigma, cc, 0), X the log-forward.  FP32 (g-table):
+// c = (sigma, G, H, 2^(t cc)) and X = X~ (see the header: the drift term is 1/d').
 template <bool GT, typename T>
 __device__ __forceinline__ void lmm_update(T &X, const typename LmmMath<T>::C c, T &W) {
     const T e = LmmMath<T>::expb(-X);
-    const T a = LmmMath<T>::rcp(GT ? fmaT(e, c.z, T(1)) : T(1) + e);   // delta L / (1 + delta L), old L
-    W = fmaT(c.y, a, W);                                                 // drift through j = n
-    X = GT ? fmaT(c.x, W, X) : fmaT(c.x, W, X) + c.z;
+    if constexpr (sizeof(T) == 4) {
+        static_assert(GT, "FP32 log-Euler strips read the g-table or the pair table");
+        W += LmmMath<T>::rcp(fmaT(e, c.y, c.z));   // h sigma delta L / (1 + delta L)
+        X = fmaT(c.x, W, X);
+    } else {
+        const T a = LmmMath<T>::rcp(T(1) + e);   // delta L / (1 + delta L), old L
+        W = fmaT(c.y, a, W);                     // drift through j = n
+        X = fmaT(c.x, W, X) + c.z;
+    }
 }
 
 // One forward of one path under the Euler scheme (eq. L_n_discrete), X = delta L:
@@ -94,17 +123,18 @@ __device__ __forceinline__ void lmm_update_euler(T &X, const typename LmmMath<T>
     X = fmaT(X * c.x, W, X);
 }
 
-// The same forward for two lockstep paths with one reciprocal: t = h sigma / (d0 d1), so
-// h sigma a_0 = t d1 and h sigma a_1 = t d0.
+// The same forward for two lockstep FP32 paths with one reciprocal: r = 1 / (d0' d1'), so the
+// drift terms are r d1' and r d0'.
 template <bool GT, typename T>
 __device__ __forceinline__ void lmm_update2(T &X0, T &X1, const typename LmmMath<T>::C c, T &W0, T &W1) {
+    static_assert(sizeof(T) == 4 && GT, "lockstep pairs share reciprocals in FP32 g-table strips");
     const T e0 = LmmMath<T>::expb(-X0), e1 = LmmMath<T>::expb(-X1);
-    const T d0 = GT ? fmaT(e0, c.z, T(1)) : T(1) + e0, d1 = GT ? fmaT(e1, c.z, T(1)) : T(1) + e1;
-    const T t = c.y * LmmMath<T>::rcp(d0 * d1);
-    W0 = fmaT(t, d1, W0);
-    W1 = fmaT(t, d0, W1);
-    X0 = GT ? fmaT(c.x, W0, X0) : fmaT(c.x, W0, X0) + c.z;
-    X1 = GT ? fmaT(c.x, W1, X1) : fmaT(c.x, W1, X1) + c.z;
+    const T d0 = fmaT(e0, c.y, c.z), d1 = fmaT(e1, c.y, c.z);
+    const T r = LmmMath<T>::rcp(d0 * d1);
+    W0 = fmaT(r, d1, W0);
+    W1 = fmaT(r, d0, W1);
+    X0 = fmaT(c.x, W0, X0);
+    X1 = fmaT(c.x, W1, X1);
 }
 
 template <typename T>
@@ -128,10 +158,15 @@ struct LmmScal {
 };
 
 // Constants in shared memory: with the g-table [NF + 1 steps][NF forwards], row t holding
-// (sigma_n, h sigma_n, 2^(-t cc_n), 2^(t cc_n)); otherwise [NF] of (sigma_n, h sigma_n, cc_n, 0).
+// (sigma_n, G = 2^(-t cc_n) H, H, 2^(t cc_n)), H = 1 / (h sigma_n); with the pair table
+// [NF/2] float4 (sigma_2q, H_2q, sigma_2q+1, H_2q+1), [NF + 1][NF/2] float2 (G_2q, G_2q+1) and
+// [NF] float 2^((t+1) cc_t); otherwise [NF] of (sigma_n, h sigma_n, cc_n, 0) (FP64, Euler scheme).
+// The Euler scheme reads the first NF entries of the region in that last layout.
 template <int NF, typename T>
-__host__ __device__ constexpr size_t lmm_cst_count() {
-    return lmm_gtab<NF, T>() ? (size_t)NF * (NF + 1) : (size_t)NF;   // the Euler scheme uses the first NF
+__host__ __device__ constexpr size_t lmm_cst_count() {   // in units of LmmMath<T>::C
+    return lmm_gtab<NF, T>()   ? (size_t)NF * (NF + 1)   // the Euler scheme uses the first NF
+           : lmm_ptab<NF, T>() ? (size_t)NF / 2 + (size_t)(NF + 1) * NF / 4 + (size_t)NF / 4
+                               : (size_t)NF;
 }
 
 // Fill the constants and the initial state X0 (all threads of the CTA; the caller synchronises).
@@ -142,8 +177,22 @@ __device__ __forceinline__ void lmm_fill_constants(const LmmModel<T> &md, typena
         for (int k = threadIdx.x; k < NF * (NF + 1); k += blockDim.x) {
             const int t = k / NF, n = k % NF;
             const float x = (float)t * md.cc[n];   // t cc_n in log2 units
-            cst[k] = CC{md.sig[n], md.hc * md.sig[n], exp2f(-x), exp2f(x)};
+            const float H = lmm_fold_inv(md.hc * md.sig[n]);
+            cst[k] = CC{md.sig[n], exp2f(-x) * H, H, exp2f(x)};
         }
+    } else if constexpr (lmm_ptab<NF, T>() && !EU) {
+        constexpr int NP = NF / 2;
+        float2 *gt = reinterpret_cast<float2 *>(cst + NP);
+        float *wf = reinterpret_cast<float *>(gt + (NF + 1) * NP);
+        for (int q = threadIdx.x; q < NP; q += blockDim.x)
+            cst[q] = CC{md.sig[2 * q], lmm_fold_inv(md.hc * md.sig[2 * q]), md.sig[2 * q + 1],
+                        lmm_fold_inv(md.hc * md.sig[2 * q + 1])};
+        for (int k = threadIdx.x; k < (NF + 1) * NP; k += blockDim.x) {
+            const int t = k / NP, q = k % NP;
+            gt[k] = make_float2(exp2f(-(float)t * md.cc[2 * q]) * lmm_fold_inv(md.hc * md.sig[2 * q]),
+                                exp2f(-(float)t * md.cc[2 * q + 1]) * lmm_fold_inv(md.hc * md.sig[2 * q + 1]));
+        }
+        for (int t = threadIdx.x; t < NF; t += blockDim.x) wf[t] = exp2f((float)(t + 1) * md.cc[t]);
     } else {
         for (int k = threadIdx.x; k < NF; k += blockDim.x) cst[k] = CC{md.sig[k], md.hc * md.sig[k], md.cc[k], T(0)};
     }
@@ -199,6 +248,13 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
     using CC = typename M::C;
     constexpr int PAD = M::PAD;
     constexpr bool GT = lmm_gtab<NF, T>() && !EU;
+    constexpr bool PG = lmm_ptab<NF, T>() && !EU;
+    static_assert(!PG || P == 1, "the pair table serves one path per thread");
+    constexpr int NP = NF / 2;
+    // pair table (PG): static pair constants, per-step G pairs, fixing factors
+    const float4 *pc = reinterpret_cast<const float4 *>(cst);
+    const float2 *pgt = reinterpret_cast<const float2 *>(pc + NP);
+    const float *pwf = reinterpret_cast<const float *>(pgt + (size_t)(NF + 1) * NP);
     const int nf = sc.nf, nK = sc.nK;
     const T sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
     const int zs = P * blockDim.x;   // stride of one step in the normals buffer
@@ -257,15 +313,30 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
 #pragma unroll
             for (int p = 0; p < P; ++p) W[p] = sqhc * zbb[tp * zs + p * blockDim.x];
             const CC *cb = GT ? cb0 + (size_t)(8 * b + tp) * NF : cb0;   // this step's row
+            const float4 *pcb = pc + 4 * b;                                // PG: pairs of the block's slots
+            const float2 *pgr = pgt + (size_t)(8 * b + tp) * NP + 4 * b;   // PG: this step's G pairs
+            // PG, one slot k of the block: (sigma, H) and G from its pair's entries
+            auto update_slot_pg = [&](const int k) {
+                if constexpr (PG) {
+                    const float4 c4 = M::lds(pcb + (k >> 1));
+                    const float2 g2 = M::lds2(pgr + (k >> 1));
+                    const float sg = (k & 1) ? c4.z : c4.x, H = (k & 1) ? c4.w : c4.y, G = (k & 1) ? g2.y : g2.x;
+                    T &x = X[0][k];
+                    W[0] += M::rcp(fmaT(M::expb(-x), G, H));
+                    x = fmaT(sg, W[0], x);
+                }
+            };
             // slot k of the P paths: FP32 pairs share a reciprocal, an odd path goes alone
             auto update_slot = [&](const int k, const CC c) {
                 if constexpr (EU) {
 #pragma unroll
                     for (int p = 0; p < P; ++p) lmm_update_euler<T>(X[p][k], c, W[p]);
                 } else if constexpr (sizeof(T) == 4) {
+                    if constexpr (GT) {
 #pragma unroll
-                    for (int p = 0; p + 1 < P; p += 2) lmm_update2<GT, T>(X[p][k], X[p + 1][k], c, W[p], W[p + 1]);
-                    if constexpr (P % 2 == 1) lmm_update<GT, T>(X[P - 1][k], c, W[P - 1]);
+                        for (int p = 0; p + 1 < P; p += 2) lmm_update2<GT, T>(X[p][k], X[p + 1][k], c, W[p], W[p + 1]);
+                        if constexpr (P % 2 == 1) lmm_update<GT, T>(X[P - 1][k], c, W[P - 1]);
+                    }
                 } else {
 #pragma unroll
                     for (int p = 0; p < P; ++p) lmm_update<GT, T>(X[p][k], c, W[p]);
@@ -273,10 +344,14 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
             };
             // group 0: alive slots tp..7, entered through a fall-through switch
             switch (tp) {
-#define RQMC_G0(k)                       \
-    case (k): {                          \
-        const CC c = M::lds(cb + (k));   \
-        update_slot(k, c);               \
+#define RQMC_G0(k)                           \
+    case (k): {                              \
+        if constexpr (PG) {                  \
+            update_slot_pg(k);               \
+        } else {                             \
+            const CC c = M::lds(cb + (k));   \
+            update_slot(k, c);               \
+        }                                    \
     }
                 RQMC_G0(0) RQMC_G0(1) RQMC_G0(2) RQMC_G0(3) RQMC_G0(4) RQMC_G0(5) RQMC_G0(6) RQMC_G0(7)
 #undef RQMC_G0
@@ -286,21 +361,22 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
 #pragma unroll
             for (int gi = 1; gi < NF / 8; ++gi) {
                 if (gi < ngrp) {
-                    if constexpr (P == 1 && sizeof(T) == 4 && SEQ != kPhilox && !EU) {
-                        // one path: adjacent forwards share a reciprocal, 1/d_k = d_(k+1) r and
-                        // 1/d_(k+1) = d_k r with r = 1/(d_k d_(k+1)).  (Not for Philox: its cached
-                        // counter words already press these strips' registers.)
+                    if constexpr (PG) {
+                        // one path: adjacent forwards share a reciprocal, 1/d'_k = d'_(k+1) r and
+                        // 1/d'_(k+1) = d'_k r with r = 1/(d'_k d'_(k+1))
 #pragma unroll
                         for (int k = 0; k < 8; k += 2) {
-                            const CC c0 = M::lds(cb + 8 * gi + k), c1 = M::lds(cb + 8 * gi + k + 1);
+                            static_assert(sizeof(T) == 4, "pair table in FP32 only");
+                            const float4 c4 = M::lds(pcb + 4 * gi + (k >> 1));
+                            const float2 g2 = M::lds2(pgr + 4 * gi + (k >> 1));
                             T &x0 = X[0][8 * gi + k], &x1 = X[0][8 * gi + k + 1];
-                            const T e0 = M::expb(-x0), e1 = M::expb(-x1);
-                            const T d0 = GT ? fmaT(e0, c0.z, T(1)) : T(1) + e0, d1 = GT ? fmaT(e1, c1.z, T(1)) : T(1) + e1;
+                            const T d0 = fmaT(M::expb(-x0), g2.x, c4.y);
+                            const T d1 = fmaT(M::expb(-x1), g2.y, c4.w);
                             const T r = M::rcp(d0 * d1);
-                            W[0] = fmaT(c0.y * r, d1, W[0]);
-                            x0 = GT ? fmaT(c0.x, W[0], x0) : fmaT(c0.x, W[0], x0) + c0.z;
-                            W[0] = fmaT(c1.y * r, d0, W[0]);
-                            x1 = GT ? fmaT(c1.x, W[0], x1) : fmaT(c1.x, W[0], x1) + c1.z;
+                            W[0] = fmaT(r, d1, W[0]);
+                            x0 = fmaT(c4.x, W[0], x0);
+                            W[0] = fmaT(r, d0, W[0]);
+                            x1 = fmaT(c4.z, W[0], x1);
                         }
                     } else {
 #pragma unroll
@@ -327,10 +403,12 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
             }
             T Lf[P], dd[P];
             // with the g-table the fixed forward's X_n = X~_n + (t+1) cc_n: one more factor 2^((t+1) cc_n)
-            const T gfix = GT ? cst[(size_t)(8 * b + tp + 1) * NF + 8 * b + tp].w : T(1);
+            T gfix = T(1);
+            if constexpr (GT) gfix = cst[(size_t)(8 * b + tp + 1) * NF + 8 * b + tp].w;
+            if constexpr (PG) gfix = pwf[8 * b + tp];
 #pragma unroll
             for (int p = 0; p < P; ++p) {
-                const T e = EU ? Xf[p] : (GT ? M::expb(Xf[p]) * gfix : M::expb(Xf[p]));   // delta L
+                const T e = EU ? Xf[p] : ((GT || PG) ? M::expb(Xf[p]) * gfix : M::expb(Xf[p]));   // delta L
                 disc[p] *= M::rcp(T(1) + e);
                 Lf[p] = e * inv_dl;
                 dd[p] = active[p] ? dl * disc[p] : T(0);
