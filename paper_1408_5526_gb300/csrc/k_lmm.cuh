@@ -220,6 +220,11 @@ __host__ __device__ __forceinline__ size_t lmm_smem_layout(const GenParams &g, i
     return off;
 }
 
+// Strips of at least this many forward slots keep the step loop of a block rolled.
+#ifndef RQMC_LMM_ROLL_MIN_NF
+#define RQMC_LMM_ROLL_MIN_NF 80
+#endif
+
 // CTAs per SM to plan registers for: forwards take NF (FP32) or 2 NF (FP64) registers.
 #ifndef RQMC_LMM_EXTRA_REGS
 #define RQMC_LMM_EXTRA_REGS 44
@@ -307,8 +312,10 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
                 }
             }
         }
-        // phase B: forward updates and payoffs (each thread reads back its own columns)
-        for (int tp = 0; tp < nst; ++tp) {
+        // phase B: forward updates and payoffs (each thread reads back its own columns).  The
+        // step loop of the wider strips stays rolled: eight copies of an 80- or 160-slot update
+        // body would overflow the instruction cache.
+        auto step = [&](const int tp) {
             T W[P];
 #pragma unroll
             for (int p = 0; p < P; ++p) W[p] = sqhc * zbb[tp * zs + p * blockDim.x];
@@ -423,6 +430,12 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
                 }
                 row[kk * PAD] = pay;
             }
+        };
+        if constexpr (NF >= RQMC_LMM_ROLL_MIN_NF) {
+#pragma unroll 1
+            for (int tp = 0; tp < nst; ++tp) step(tp);
+        } else {
+            for (int tp = 0; tp < nst; ++tp) step(tp);
         }
         __syncwarp();
         const int nrows = nst * nK;
