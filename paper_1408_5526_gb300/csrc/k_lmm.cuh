@@ -244,7 +244,9 @@ constexpr int lmm_min_blocks() {
 // ZG: the normals are not generated here but read from zg, the replication's normals
 // [step][N] written beforehand by the point-stream kernel from the plan's own generator:
 // path i takes zg[t N + i], copied into the thread's shared columns a block ahead.
-template <int NF, int SEQ, typename T, int P, bool EU = false, bool ZG = false>
+// DK: Ks holds delta K and the payoff is (delta L - delta K)^+ D; otherwise Ks holds K and the
+// payoff is delta (L - K)^+ D with L = delta L / delta (the same value up to rounding).
+template <int NF, int SEQ, typename T, int P, bool EU = false, bool ZG = false, bool DK = true>
 __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&active)[P], const LmmScal<T> &sc,
                                          const typename LmmMath<T>::C *cst, const T *X0, const T *Ks, T *zb,
                                          T *wbuf, T *wacc, T *wcmp, const int lane, const T *zg = nullptr,
@@ -261,7 +263,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
     const float2 *pgt = reinterpret_cast<const float2 *>(pc + NP);
     const float *pwf = reinterpret_cast<const float *>(pgt + (size_t)(NF + 1) * NP);
     const int nf = sc.nf, nK = sc.nK;
-    const T sqhc = sc.sqhc, inv_dl = sc.inv_dl, dl = sc.dl;
+    const T sqhc = sc.sqhc;
     const int zs = P * blockDim.x;   // stride of one step in the normals buffer
     T X[P][NF];
 #pragma unroll
@@ -408,6 +410,7 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
                 default:
                     break;
             }
+            // DK: the payoff delta (L - K)^+ D as (delta L - delta K)^+ D, strikes staged as delta K
             T Lf[P], dd[P];
             // with the g-table the fixed forward's X_n = X~_n + (t+1) cc_n: one more factor 2^((t+1) cc_n)
             T gfix = T(1);
@@ -417,8 +420,13 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
             for (int p = 0; p < P; ++p) {
                 const T e = EU ? Xf[p] : ((GT || PG) ? M::expb(Xf[p]) * gfix : M::expb(Xf[p]));   // delta L
                 disc[p] *= M::rcp(T(1) + e);
-                Lf[p] = e * inv_dl;
-                dd[p] = active[p] ? dl * disc[p] : T(0);
+                if constexpr (DK) {
+                    Lf[p] = e;
+                    dd[p] = active[p] ? disc[p] : T(0);
+                } else {
+                    Lf[p] = e * sc.inv_dl;
+                    dd[p] = active[p] ? sc.dl * disc[p] : T(0);
+                }
             }
             T *row = wbuf + (size_t)tp * nK * PAD + lane;
             for (int kk = 0; kk < nK; ++kk) {
@@ -490,7 +498,7 @@ __global__ void __launch_bounds__(256, lmm_min_blocks<NF, T>()) lmm_caplet_kerne
     T *cmp = acc + nw * nout;
     T *wacc = acc + warp * nout, *wcmp = cmp + warp * nout;
     lmm_fill_constants<NF, T, EU>(md, cst, X0);
-    if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md.K[threadIdx.x];
+    if (threadIdx.x < kMaxStrikes) Ks[threadIdx.x] = md.dl * md.K[threadIdx.x];   // delta K (DK payoff form)
     zero_acc(acc, cmp, nw * nout);
     const LmmScal<T> sc{md.nf, md.nK, md.dl, md.inv_dl, md.disc0, md.hc, md.sqhc};
     uint32_t u0, u1;

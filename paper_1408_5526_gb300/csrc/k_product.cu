@@ -75,21 +75,36 @@ cudaError_t launch_product(const Plan &pl, cudaStream_t st) {
 }
 
 // theta[m][o] = (sum over the tiles of replication m, in tile order) / N
-__global__ void theta_kernel(const double *__restrict__ partials, int nout, uint32_t tiles_per_m, int M, double N,
-                             double *__restrict__ theta) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= M * nout) return;
-    const int m = idx / nout, o = idx % nout;
-    const double *p = partials + (size_t)m * tiles_per_m * nout + o;
+// theta[m][o] = (sum over the replication's tiles of partials[m][tile][o]) / N.  A CTA of 32 x 8
+// threads serves 32 outputs of one replication: thread (x, y) sums the y-th contiguous eighth
+// of the tiles for output x (the 32 reads of a tile are one 256-byte row), and the eight part
+// sums are added in y order, so the result does not depend on scheduling.
+constexpr int kThetaSlices = 8;
+__global__ void __launch_bounds__(32 * kThetaSlices) theta_kernel(const double *__restrict__ partials, int nout,
+                                                                  uint32_t tiles_per_m, double N,
+                                                                  double *__restrict__ theta) {
+    __shared__ double part[kThetaSlices][32];
+    const int o = blockIdx.x * 32 + threadIdx.x, m = blockIdx.y;
+    const uint32_t t0 = (uint32_t)(((unsigned long long)threadIdx.y * tiles_per_m) / kThetaSlices);
+    const uint32_t t1 = (uint32_t)(((unsigned long long)(threadIdx.y + 1) * tiles_per_m) / kThetaSlices);
     double s = 0.0;
-    for (uint32_t t = 0; t < tiles_per_m; ++t) s += p[(size_t)t * nout];
-    theta[idx] = s / N;
+    if (o < nout) {
+        const double *p = partials + (size_t)m * tiles_per_m * nout + o;
+        for (uint32_t t = t0; t < t1; ++t) s += p[(size_t)t * nout];
+    }
+    part[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && o < nout) {
+        double tot = 0.0;
+#pragma unroll
+        for (int k = 0; k < kThetaSlices; ++k) tot += part[k][threadIdx.x];
+        theta[(size_t)m * nout + o] = tot / N;
+    }
 }
 
 cudaError_t launch_theta(const Plan &pl, double *theta_dev, cudaStream_t st) {
-    const int n = pl.M * pl.red.nout;
-    theta_kernel<<<(n + 255) / 256, 256, 0, st>>>(pl.red.partials, pl.red.nout, pl.red.tiles_per_m, pl.M,
-                                                   (double)pl.N, theta_dev);
+    const dim3 grid((unsigned)((pl.red.nout + 31) / 32), (unsigned)pl.M), block(32, kThetaSlices);
+    theta_kernel<<<grid, block, 0, st>>>(pl.red.partials, pl.red.nout, pl.red.tiles_per_m, (double)pl.N, theta_dev);
     return cudaGetLastError();
 }
 
