@@ -44,10 +44,11 @@ import numpy as np  # noqa: E402
 N_FWD, N_PATHS, M_REPL, SEED = 40, 65536, 64, 1
 SEQS = ("rasrap", "sobol_ds", "philox")
 L2_FLUSH_BYTES = 512 << 20
-# dram__bytes_read.sum + dram__bytes_write.sum of one lmm_caplet_kernel<40, 1, float> launch
-# (Rasrap) of this workload, from an ncu capture of the kernel as committed; None whenever
-# that kernel has changed since the capture.
-LMM_TRAFFIC_BYTES = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one plan execute of this workload (Rasrap:
+# points_run_kernel 0.7 + 609.9 MB, lmm_caplet_kernel<40> 671.2 + 11.7 MB, theta_kernel 7.9 MB),
+# from an ncu capture of the kernels as committed (profiles/lmm_caplet_kernel_40fwd_N65536_M64.md);
+# None whenever one of them has changed since the capture.
+LMM_TRAFFIC_BYTES = 1301.4e6
 
 
 def _peaks():
@@ -288,8 +289,9 @@ def run_ours(args, rank, world):
     roof = pk.alu(mufu, fma, per_launch_s, "one plan execute: points_run_kernel normals + "
                   "lmm_caplet_kernel<40,float> (normals loaded) + theta_kernel")
     roof.update({"traffic": LMM_TRAFFIC_BYTES,
-                 "traffic_unit": "DRAM bytes per launch (ncu, Rasrap launch; tables only)" if LMM_TRAFFIC_BYTES
-                 else "not captured since the kernel last changed",
+                 "traffic_unit": ("DRAM bytes per plan execute (ncu, Rasrap, kernels replayed cold): the FP32 "
+                                  "normals' round trip through HBM, 0 algorithmic bytes") if LMM_TRAFFIC_BYTES
+                 else "not captured since the kernels last changed",
                  "launch_ms": round(per_launch_s * 1e3, 4),
                  "probe_per_sm_clk": {k: round(v, 2) for k, v in probe.items()}})
     # the same pipes measured on this GPU: one slot = one rcp or lg2 = two ex2
