@@ -63,11 +63,12 @@ __host__ __device__ __forceinline__ size_t adj_smem_layout(const GenParams &g, s
     return off;
 }
 
-// The shared-memory state columns limit residency to 2 CTAs per SM for the staged sequences,
-// so a budget of up to 128 registers costs no occupancy and lets each chunk keep its loads
-// and SFU results in flight.
+// The shared-memory state columns (NF floats per thread, 40 KB per 128-thread CTA at 80
+// forwards) allow five CTAs per SM; the register budget that five CTAs leave (102 per thread)
+// holds the kernel without spills.  Measured on the Greeks workload: 20 warps per SM at 128
+// threads per CTA ran 5 % faster than 16 warps at 256.
 #ifndef RQMC_ADJ_MIN_BLOCKS
-#define RQMC_ADJ_MIN_BLOCKS 2
+#define RQMC_ADJ_MIN_BLOCKS 5
 #endif
 
 // ZG: the normals are read from zg ([M][D nf][N], written beforehand by the point-stream run

@@ -211,7 +211,9 @@ int64_t batch_output_size(const Plan &pl);
 void batch_destroy(Plan &pl);
 int batch_ppt(const Plan &pl);
 int adjoint_grid(const Plan &pl);
-constexpr int kAdjointThreads = 256;   // CTA size of the adjoint kernel
+// CTA size of the adjoint kernel: 128 threads, so that five CTAs (20 warps) fit the shared
+// memory of an SM with the per-thread state columns of an 80-forward strip.
+constexpr int kAdjointThreads = 128;
 int occupancy_blocks(const Plan &pl);
 
 // ---- the caller's initial curve as forwards (eq. BL for bond prices); p points into itself
