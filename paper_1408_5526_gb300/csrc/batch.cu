@@ -72,10 +72,14 @@ static size_t item_smem(const BatchInst &bi, int threads) {
     if (bi.kind == 0) {
         size_t a, b, c, d, e;
         switch (bi.bucket) {
-            case 16: return lmm_smem_layout<16, float, batch_ilp<16>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
-            case 40: return lmm_smem_layout<40, float, batch_ilp<40>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
-            case 80: return lmm_smem_layout<80, float, batch_ilp<80>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
-            default: return lmm_smem_layout<160, float, batch_ilp<160>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e);
+            case 16: return lmm_smem_layout<16, float, batch_ilp<16>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e,
+                                                                        batch_zg<16>() ? 2 : 1);
+            case 40: return lmm_smem_layout<40, float, batch_ilp<40>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e,
+                                                                        batch_zg<40>() ? 2 : 1);
+            case 80: return lmm_smem_layout<80, float, batch_ilp<80>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e,
+                                                                        batch_zg<80>() ? 2 : 1);
+            default: return lmm_smem_layout<160, float, batch_ilp<160>()>(bi.g, nw, 1, bi.nout, &a, &b, &c, &d, &e,
+                                                                          batch_zg<160>() ? 2 : 1);
         }
     }
     return stage_bytes(bi.g) + sizeof(float) * (2 * (size_t)nw + (size_t)bi.g.s + 1);
@@ -155,6 +159,20 @@ static rqmc_status setup_launch(BatchPlan &bp, int threads, int ppt, bool cap_n)
     const size_t o_stats = cv.take(sizeof(unsigned long long) * 3 * kBatchClasses * stats_cap);
     const size_t o_part = cv.take(sizeof(double) * part);
     const size_t o_theta = cv.take(sizeof(double) * theta);
+    // normals buffers of the strip classes: one per CTA of the persistent grid (one CTA per SM
+    // in class 0, two in class 2: their register budgets), the class's largest bucket x the tile
+    const uint32_t tile = (uint32_t)(threads * ppt);
+    int zbucket[kBatchClasses] = {};
+    for (const BatchInst &bi : insts)
+        if (bi.kind == 0 && batch_zg_bucket(bi.bucket)) zbucket[batch_class(bi)] = std::max(zbucket[batch_class(bi)], bi.bucket);
+    size_t o_z[kBatchClasses] = {}, zstride[kBatchClasses] = {};
+    uint32_t zctas[kBatchClasses] = {};
+    for (int k = 0; k < kBatchClasses; ++k) {
+        if (!zbucket[k] || items[k].empty()) continue;
+        zctas[k] = (uint32_t)std::max(sms, 1) * (k == 0 ? 1u : 2u);
+        zstride[k] = (size_t)zbucket[k] * tile;
+        o_z[k] = cv.take(sizeof(float) * zstride[k] * zctas[k]);
+    }
     cudaError_t e = cudaMalloc(&bp.d_work, cv.off);
     if (e != cudaSuccess) { bp.d_work = nullptr; set_error("batch: work allocation failed"); return RQMC_ENOMEM; }
     unsigned char *d = static_cast<unsigned char *>(bp.d_work);
@@ -182,6 +200,11 @@ static rqmc_status setup_launch(BatchPlan &bp, int threads, int ppt, bool cap_n)
     bl.theta = reinterpret_cast<double *>(d + o_theta);
     bl.threads = threads;
     bl.ppt = ppt;
+    for (int k = 0; k < kBatchClasses; ++k) {
+        bl.znorm[k] = zctas[k] ? reinterpret_cast<float *>(d + o_z[k]) : nullptr;
+        bl.zstride[k] = zstride[k];
+        bl.zctas[k] = zctas[k];
+    }
     bl.fork = bp.fork;
     for (int k = 0; k + 1 < kBatchClasses; ++k) {
         bl.side[k] = bp.side[k];

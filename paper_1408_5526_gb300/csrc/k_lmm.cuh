@@ -241,16 +241,17 @@ constexpr int lmm_min_blocks() {
 // the P paths) into the warp's transpose buffer, block sums into the warp's Kahan
 // accumulators (wacc/wcmp, indexed by output t nK + k).  The P paths share every constant
 // load and all control flow, and give each warp P independent dependency chains.
-// ZG: the normals are not generated here but read from zg, the replication's normals
-// [step][N] written beforehand by the point-stream kernel from the plan's own generator:
-// path i takes zg[t N + i], copied into the thread's shared columns a block ahead.
+// ZG: the normals are not generated here but read from zg, normals [step][zN] written
+// beforehand from the same generator (by the point-stream kernel for a plan's replication,
+// zi0 = 0; by the batch kernel for an item's points from zi0 on): path i takes
+// zg[t zN + i - zi0], copied into the thread's shared columns a block ahead.
 // DK: Ks holds delta K and the payoff is (delta L - delta K)^+ D; otherwise Ks holds K and the
 // payoff is delta (L - K)^+ D with L = delta L / delta (the same value up to rounding).
 template <int NF, int SEQ, typename T, int P, bool EU = false, bool ZG = false, bool DK = true>
 __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&active)[P], const LmmScal<T> &sc,
                                          const typename LmmMath<T>::C *cst, const T *X0, const T *Ks, T *zb,
                                          T *wbuf, T *wacc, T *wcmp, const int lane, const T *zg = nullptr,
-                                         size_t zN = 0) {
+                                         size_t zN = 0, uint32_t zi0 = 0) {
     using M = LmmMath<T>;
     using CC = typename M::C;
     constexpr int PAD = M::PAD;
@@ -285,7 +286,8 @@ __device__ __forceinline__ void lmm_path(PathGen<SEQ> (&pg)[P], const bool (&act
             for (int tp = 0; tp < 8; ++tp)
 #pragma unroll
                 for (int p = 0; p < P; ++p)
-                    if (tp < nb) cp_async4(dst + tp * zs + p * blockDim.x, zg + (size_t)(8 * bb + tp) * zN + pg[p].i);
+                    if (tp < nb)
+                        cp_async4(dst + tp * zs + p * blockDim.x, zg + (size_t)(8 * bb + tp) * zN + (pg[p].i - zi0));
         }
         cp_async_commit();   // an empty group past the last block keeps the wait count uniform
     };

@@ -128,6 +128,11 @@ struct BatchLaunch {
     uint32_t stats_cap;
     int threads, ppt;
     size_t smem[kBatchClasses];
+    // per-CTA normals buffers of the strip classes (0 and 2): zctas CTAs of zstride floats
+    // (the largest bucket of the class x the tile); the class's grid never exceeds zctas
+    float *znorm[kBatchClasses];
+    size_t zstride[kBatchClasses];
+    uint32_t zctas[kBatchClasses];
     cudaStream_t side[kBatchClasses - 1];   // classes 1.. run on forked streams
     cudaEvent_t fork, join[kBatchClasses - 1];
 };
