@@ -252,6 +252,10 @@ rqmc_status rqmc_plan_batch_stats(rqmc_plan *plan, double *out_host, int n);
 int rqmc_plan_launches(const rqmc_plan *plan);
 /* Tuning knobs of a plan: threads per block and paths per thread (0 = keep). */
 rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int paths_per_thread);
+/* The plan's launch shape (not in the paper): threads per block and paths per thread, for a
+ * batch plan the tile its autotuner chose or read from its cache.  Host-only, no GPU work;
+ * RQMC_EINVAL for a NULL argument. */
+rqmc_status rqmc_plan_get_launch(const rqmc_plan *plan, int *threads, int *paths_per_thread);
 /* Launch the plan's kernels on `stream` (asynchronous), writing rqmc_plan_output_size(plan)
  * values to device memory `theta_dev`, which the caller owns and must size; the device the
  * plan was built on must be current (RQMC_EINVAL otherwise, nothing launched). */

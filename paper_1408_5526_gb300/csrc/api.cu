@@ -389,6 +389,13 @@ extern "C" int64_t rqmc_plan_output_size(const rqmc_plan *plan) {
 
 extern "C" int rqmc_plan_launches(const rqmc_plan *plan) { return plan ? plan->launches : 0; }
 
+extern "C" rqmc_status rqmc_plan_get_launch(const rqmc_plan *plan, int *threads, int *paths_per_thread) {
+    if (!plan || !threads || !paths_per_thread) { set_error("plan and both outputs are required"); return RQMC_EINVAL; }
+    *threads = plan->threads;
+    *paths_per_thread = plan->ppt;
+    return RQMC_OK;
+}
+
 extern "C" rqmc_status rqmc_plan_set_launch(rqmc_plan *plan, int threads, int paths_per_thread) {
     if (!plan) { set_error("plan is NULL"); return RQMC_EINVAL; }
     if (plan->kind == kAdjoint || plan->kind == kBatch || plan->kind == kPoints) {

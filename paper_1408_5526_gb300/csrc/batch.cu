@@ -5,7 +5,8 @@
 //
 // The autotuner times the captured launch for several tile sizes (paths per thread) on a
 // copy of the batch with N capped at 8192 per instrument and keeps the fastest; the choice
-// is cached in a small JSON file keyed by GPU name, sequence and a hash of the batch
+// (and each candidate's time in microseconds, under "<key>|us_ppt<k>") is cached in a
+// small JSON file keyed by GPU name, sequence and a hash of the batch
 // (path: $RQMC_AUTOTUNE_CACHE, default ~/.cache/rqmc_gb300/autotune.json;
 // RQMC_AUTOTUNE=0 skips tuning and uses 4 paths per thread).
 #include <algorithm>
@@ -312,6 +313,7 @@ static int autotune(BatchPlan &bp) {
     for (int ppt : {4, 8, 16}) {   // multiples of every bucket's paths per thread in lockstep
         if (setup_launch(bp, 256, ppt, true) != RQMC_OK) continue;
         const float ms = time_launch(bp);
+        kv[key + "|us_ppt" + std::to_string(ppt)] = (int)std::lround(1000.0 * ms);   // the candidate's time
         if (ms < best_ms) { best_ms = ms; best = ppt; }
     }
     kv[key] = best;

@@ -34,7 +34,7 @@ EXPORTS = ["rqmc_set_sobol_table", "rqmc_points", "rqmc_integrate_product", "pri
            "rqmc_plan_adjoint", "rqmc_plan_batch", "rqmc_plan_output_size", "rqmc_plan_launches",
            "rqmc_plan_set_launch", "rqmc_plan_execute", "rqmc_plan_check", "rqmc_plan_destroy",
            "rqmc_status_string", "rqmc_last_error", "rqmc_abi_version", "rqmc_price_caplets_noalloc",
-           "rqmc_plan_points", "rqmc_probe_pipes", "rqmc_plan_batch_stats"]
+           "rqmc_plan_points", "rqmc_probe_pipes", "rqmc_plan_batch_stats", "rqmc_plan_get_launch"]
 
 
 class RqmcError(RuntimeError):
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         L.rqmc_plan_output_size.restype = i64
         L.rqmc_plan_launches.argtypes = [vp]
         L.rqmc_plan_set_launch.argtypes = [vp, C.c_int, C.c_int]
+        L.rqmc_plan_get_launch.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.rqmc_plan_execute.argtypes = [vp, dp, vp]
         L.rqmc_plan_check.argtypes = [vp, vp]
         L.rqmc_plan_destroy.argtypes = [vp]
@@ -395,6 +396,14 @@ class Plan:
 
     def launches(self):
         return int(load().rqmc_plan_launches(self._h))
+
+    def launch_shape(self):
+        """(threads per block, paths per thread) the plan launches with (a batch plan: the
+        autotuner's tile)."""
+        L = load()
+        t, p = C.c_int(), C.c_int()
+        _check(L, L.rqmc_plan_get_launch(self._h, C.byref(t), C.byref(p)))
+        return t.value, p.value
 
     def set_launch(self, threads=0, paths_per_thread=0):
         _check(load(), load().rqmc_plan_set_launch(self._h, threads, paths_per_thread))

@@ -75,6 +75,36 @@ def test_batch_graph_replay_is_deterministic_and_cached(R):
     assert [x.shape for x in parts] == [(3, d["n_fwd"] if d["kind"] == "lmm" else 1) for d in INSTS]
 
 
+def test_batch_autotuner_keeps_the_fastest_tile_and_reuses_its_cache(R, tmp_path, monkeypatch):
+    """The autotuner times the three candidate tiles, keeps the fastest (recorded in its cache
+    with every candidate's time) and a later plan of the same batch takes the cached tile."""
+    import json
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("RQMC_AUTOTUNE_CACHE", str(cache))
+    monkeypatch.delenv("RQMC_AUTOTUNE", raising=False)
+    insts = INSTS[:3]
+    p = R.Plan.batch(insts, 2, O.SOBOL_DS, 7)
+    threads, ppt = p.launch_shape()
+    p.close()
+    kv = json.loads(cache.read_text())
+    keys = [k for k in kv if "|us_ppt" not in k]
+    assert len(keys) == 1 and kv[keys[0]] == ppt and threads == 256
+    times = {int(k.rsplit("ppt", 1)[1]): v for k, v in kv.items() if k.startswith(keys[0] + "|us_ppt")}
+    assert sorted(times) == [4, 8, 16]
+    assert times[ppt] == min(times.values())
+    # a different tile written into the cache is taken as it stands: no tuning, same batch key
+    other = next(c for c in (16, 8, 4) if c != ppt)
+    kv[keys[0]] = other
+    cache.write_text(json.dumps(kv, indent=2))   # the cache keeps one "key": value entry per line
+    q = R.Plan.batch(insts, 2, O.SOBOL_DS, 7)
+    assert q.launch_shape() == (256, other)
+    got = q.split_batch(q.execute())
+    q.close()
+    ref = _oracle(O.SOBOL_DS, 2, 7, insts)
+    for d, g, r in zip(insts, got, ref):
+        assert np.all(np.abs(g - r) <= 1e-4 * np.abs(r)), (d, np.max(np.abs(g - r) / np.abs(r)))
+
+
 @pytest.mark.parametrize("subset", [[1, 4], [0, 2, 3], [5, 6], [6, 1]])
 def test_batch_with_some_work_classes_empty(R, subset):
     """Batches that leave one or two of the three work classes empty (MBS only, small
