@@ -346,7 +346,7 @@ extern "C" rqmc_status rqmc_plan_mbs(const rqmc_mbs_params *p, int64_t N, int64_
     rqmc_plan *pl = nullptr;
     rs = new_plan(kMbs, p->months, N, offset, M, seq, seed, prec, &pl);
     if (rs != RQMC_OK) return rs;
-    set_reduction(*pl, 1, 256, prec == RQMC_FP32 ? 2 : 1);   // FP32: two lockstep paths per thread
+    set_reduction(*pl, 1, 256, prec == RQMC_FP32 ? mbs_paths32(seq) : 1);   // FP32: lockstep paths per thread
     const int Mm = p->months;
     const double v = 1.0 / (1.0 + p->i0);
     std::vector<double> ck(Mm + 1, 0.0);

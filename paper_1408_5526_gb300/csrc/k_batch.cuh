@@ -18,13 +18,13 @@ namespace rqmc {
 
 // Paths per thread in lockstep per bucket, sized to the register budget of the bucket's
 // work class (16/40/80 forwards: 2 CTAs per SM, 128 registers; 160: 1 CTA per SM).  MBS
-// paths go two per thread, as in the MBS kernel: their coordinates and the central
-// inverse-CDF branch are generated together.
+// paths go mbs_paths32(SEQ) per thread, as in the MBS kernel: their coordinates and the
+// central inverse-CDF branch are generated together.
 template <int NF>
 __host__ __device__ constexpr int batch_ilp() {
     return NF <= 16 ? 4 : NF <= 40 ? 2 : 1;
 }
-constexpr int kBatchMbsIlp = 2;
+
 
 // Work class of an instrument (see BatchLaunch).
 __host__ __device__ inline int batch_class(const BatchInst &bi) { return bi.kind != 0 ? 1 : bi.bucket == 160 ? 0 : 2; }
@@ -125,7 +125,7 @@ __device__ __forceinline__ void batch_mbs(const BatchInst &bi, const BatchItem &
     for (int k = threadIdx.x; k <= md.months; k += blockDim.x) ck[k] = md.ck[k];
     zero_acc(acc, cmp, nw);
     __syncthreads();
-    constexpr int P = kBatchMbsIlp;
+    constexpr int P = mbs_paths32(SEQ);
     for (int pp = 0; pp < r.ppt; pp += P) {
         PathGen<SEQ> pg[P];
         bool act[P];

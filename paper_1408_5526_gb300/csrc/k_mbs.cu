@@ -9,16 +9,16 @@
 
 namespace rqmc {
 
-// Paths per thread in lockstep: two in FP32 (their coordinates share the dimension's
-// constants, and a Sobol' point blockDim away costs a few XORs), one in FP64.
-template <typename T>
+// Paths per thread in lockstep: in FP32 mbs_paths32(SEQ) (their coordinates share the
+// dimension's constants, and a Sobol' point blockDim away costs a few XORs), one in FP64.
+template <typename T, int SEQ>
 constexpr int mbs_ilp() {
-    return sizeof(T) == 4 ? 2 : 1;
+    return sizeof(T) == 4 ? mbs_paths32(SEQ) : 1;
 }
 
 template <typename T, int SEQ, bool STAGED>
 __global__ void __launch_bounds__(256) mbs_kernel(const GenParams g, const MbsModel<T> md, const RedParams r) {
-    constexpr int P = mbs_ilp<T>();
+    constexpr int P = mbs_ilp<T, SEQ>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nw = blockDim.x >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T *acc = reinterpret_cast<T *>(smem_raw + stage_bytes(g));

@@ -216,6 +216,12 @@ int64_t batch_output_size(const Plan &pl);
 void batch_destroy(Plan &pl);
 int batch_ppt(const Plan &pl);
 int adjoint_grid(const Plan &pl);
+// Paths per thread in lockstep in the FP32 MBS kernels (the MBS plans' paths per thread per
+// unit): four for Sobol' (the three extra points cost a few XORs of direction numbers each),
+// two for Halton, Rasrap and Philox.  Measured on the MBS workload (360 months, N = 65536,
+// M = 64): four lockstep paths took Sobol' from 5.50 to 4.68 ms but Rasrap from 6.18 to 6.69 ms.
+__host__ __device__ constexpr int mbs_paths32(int seq) { return seq == 2 || seq == 4 ? 4 : 2; }   // kSobolDS, kSobolLMS
+
 // CTA size of the adjoint kernel: 128 threads, so that five CTAs (20 warps) fit the shared
 // memory of an SM with the per-thread state columns of an 80-forward strip.
 constexpr int kAdjointThreads = 128;
