@@ -102,10 +102,17 @@ __device__ __forceinline__ unsigned long long high_numerator(unsigned long long 
     return num;
 }
 
-__global__ void setup_halton_kernel(const BaseConst *__restrict__ bases, int s, int M, uint32_t key0, uint32_t key1,
-                                    uint32_t inst, unsigned long long offset, unsigned long long N, int identity,
-                                    HaltonDim *__restrict__ hdim, uint16_t *__restrict__ sigma,
-                                    unsigned long long sig_len, uint32_t *status) {
+// One thread per (m, j).  Bases up to kSetupSmemP shuffle their permutation in a private
+// shared-memory row (the Fisher-Yates swaps are dependent random accesses, far slower in
+// global memory) and copy it out at the end; larger bases shuffle in place in global memory.
+constexpr uint32_t kSetupSmemP = 256;
+constexpr int kSetupThreads = 64;
+__global__ void __launch_bounds__(kSetupThreads)
+    setup_halton_kernel(const BaseConst *__restrict__ bases, int s, int M, uint32_t key0, uint32_t key1,
+                        uint32_t inst, unsigned long long offset, unsigned long long N, int identity,
+                        HaltonDim *__restrict__ hdim, uint16_t *__restrict__ sigma, unsigned long long sig_len,
+                        uint32_t *status) {
+    __shared__ uint16_t work[kSetupThreads][kSetupSmemP + kSigPad];
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= M * s) return;
     const int m = idx / s, j = idx % s;
@@ -121,7 +128,9 @@ __global__ void setup_halton_kernel(const BaseConst *__restrict__ bases, int s, 
         pw /= b.p;
     }
     // permutation
-    uint16_t *sg = sigma + (size_t)m * sig_len + b.sig_off;
+    uint16_t *const gsg = sigma + (size_t)m * sig_len + b.sig_off;
+    const bool local = b.p <= kSetupSmemP;
+    uint16_t *sg = local ? work[threadIdx.x] : gsg;
     for (uint32_t a = 0; a < b.p; ++a) sg[a] = (uint16_t)a;
     if (!identity) {
         U32x4 r4{};
@@ -136,6 +145,8 @@ __global__ void setup_halton_kernel(const BaseConst *__restrict__ bases, int s, 
         }
     }
     for (uint32_t a = 0; a < kSigPad; ++a) sg[b.p + a] = sg[a % b.p];
+    if (local)
+        for (uint32_t a = 0; a < b.p + kSigPad; ++a) gsg[a] = sg[a];
     // split of n0 + offset at digit L
     const unsigned long long n0o = n0 + offset;
     bool ok = n0o >= n0 && n0o <= b.D - N;   // n0 + offset + N - 1 < p^(K+1)
@@ -296,9 +307,9 @@ rqmc_status generator_init(Plan &pl, const GenLayout &gl, unsigned char *d, uint
         BaseConst *db = reinterpret_cast<BaseConst *>(d + gl.base_off);
         if (cudaMemcpyAsync(db, gl.bases.data(), sizeof(BaseConst) * s, cudaMemcpyHostToDevice, st) != cudaSuccess)
             return RQMC_ECUDA;
-        setup_halton_kernel<<<nblk, nthr, 0, st>>>(db, s, M, g.key0, g.key1, g.inst, pl.offset, pl.N,
-                                                   pl.seq == kHaltonRS ? 1 : 0, const_cast<HaltonDim *>(g.hdim),
-                                                   const_cast<uint16_t *>(g.sigma), gl.sig_len, d_status);
+        setup_halton_kernel<<<(M * s + kSetupThreads - 1) / kSetupThreads, kSetupThreads, 0, st>>>(
+            db, s, M, g.key0, g.key1, g.inst, pl.offset, pl.N, pl.seq == kHaltonRS ? 1 : 0,
+            const_cast<HaltonDim *>(g.hdim), const_cast<uint16_t *>(g.sigma), gl.sig_len, d_status);
     } else if (pl.seq == kSobolDS || pl.seq == kSobolLMS) {
         uint32_t *V = reinterpret_cast<uint32_t *>(d + gl.sobV_off);
         uint32_t *sh = reinterpret_cast<uint32_t *>(d + gl.shift_off);
