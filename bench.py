@@ -395,8 +395,9 @@ def other_workloads(args, dev, seed, pk):
     (cpu_baseline), the parity of the GPU result on that sample, the largest error against
     the oracle, and a roofline fraction: product integrand (FP64), LMM caplets in FP64,
     MBS (FP32), two-factor adjoint Greeks (FP32), the 512-instrument batch (FP32, graph
-    launch), the Treasury-curve study of Sec. 5 (std, time and efficiency against N), the
-    Matousek-scrambled Sobol' caplets and the point stream (HBM write GB/s)."""
+    launch), the Treasury-curve study of Sec. 5 and the MBS study of Sec. 6 (std, time and
+    efficiency against N), the Matousek-scrambled Sobol' caplets and the point stream (HBM
+    write GB/s)."""
     import torch
 
     import oracle as O
@@ -585,6 +586,35 @@ def other_workloads(args, dev, seed, pk):
                                     "checked": "N = 2^14, all 100 replications, all 10 caplets"}}
         out["lmm_treasury_study_T5_M100_fp32"] = study
 
+    if want("mbs_study"):
+        # Sec. 6 study: std of M = 64 independent MBS estimates (360 months), time and efficiency
+        # (std x time) against N, and the fitted convergence rate of the std (the paper's GPU rates:
+        # Philox ~0.5, Rasrap 0.68, Sobol' 0.86)
+        mbs = inputs.mbs_paper(360)
+        Ms = 64
+        study = {}
+        for s_ in SEQS + ("sobol_lms",):
+            rows = []
+            for e in range(10, 19, 2):
+                pt = rqmc.Plan.mbs(mbs, 1 << e, Ms, s_, seed, prec="fp32")
+                ot = torch.empty(pt.output_size(), dtype=torch.float64, device=dev)
+                ms = _time_plan(lambda: pt.execute(ot), 3, flush)
+                th = ot.cpu().numpy()
+                pt.close()
+                rows.append({"N": 1 << e, "rq": float(th.mean()), "std": float(th.std(ddof=1)), "ms": ms,
+                             "efficiency": float(th.std(ddof=1)) * ms})
+                if e == 12:   # parity at N = 2^12 on the first 8 replications
+                    sid = {"rasrap": O.RASRAP, "sobol_ds": O.SOBOL_DS, "philox": O.PHILOX, "sobol_lms": O.SOBOL_LMS}[s_]
+                    th_o = O.mbs_theta(O.Sequence(sid, 360, Ms, seed, joe_kuo=jk), mbs, 1 << e, m_range=(0, 8),
+                                       threads=T)[:8]
+                    rel12 = float(np.max(np.abs(th[:8] - th_o) / np.abs(th_o)))
+            lx = np.log([r["N"] for r in rows])
+            ly = np.log([r["std"] for r in rows])
+            study[s_] = {"rate": float(np.polyfit(lx, ly, 1)[0]), "by_N": rows,
+                         "parity": {"ok": rel12 <= 1e-4, "tol": 1e-4, "max_rel_err": rel12,
+                                    "checked": "N = 2^12, replications 0..7"}}
+        out["mbs_study_360m_M64_fp32"] = study
+
     # ---- Matousek-scrambled Sobol' on the headline caplet workload (same kernel, scrambled tables)
     if want("lms"):
         pl_ = rqmc.Plan.caplets(lm, K, N_PATHS, M_REPL, "sobol_lms", seed, prec="fp32")
@@ -698,7 +728,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the other-configuration figures")
     ap.add_argument("--extra", default="all",
                     help="comma-separated subset of the other configurations: product, fp64, mbs, adjoint, batch, "
-                         "treasury, lms, points (default all)")
+                         "treasury, mbs_study, lms, points (default all)")
     ap.add_argument("--points-m", type=int, default=M_REPL,
                     help="replications of the point-stream figure (default 64; smaller for profiler captures)")
     args = ap.parse_args()
